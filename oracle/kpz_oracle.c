@@ -1,0 +1,359 @@
+/*
+ * kpz_oracle.c -- CPU oracle for the 2+1-dimensional octahedron (KPZ) lattice model.
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is a plain, slow, single-threaded
+ * restatement of the method, used by the tests, by the smoke check and by the
+ * CPU-baseline leg of the benchmark. The product path (the CUDA library) never
+ * links, loads or calls it, and it shares no code with that path.
+ *
+ * What it follows (Kelling, Odor, Nagy, Schulz, Heinig, arXiv:1204.5072):
+ *   - Sec. 2.1, eq. (rule): octahedron slopes sigma_x, sigma_y = +-1 per site;
+ *     a local minimum is raised by 2 with probability p, a local maximum is
+ *     lowered by 2 with probability q.
+ *   - Sec. 2.1: flat start, periodic boundaries, height reconstruction from the
+ *     slopes, squared interface width W^2 (eq. Wdef).
+ *   - Sec. 3: dead-border decomposition at the device layer with a randomly moved
+ *     origin; Sec. 3.1: single-hit double tiling at the work-group layer (four
+ *     sets of cells, one random set per round, one attempt per active cell,
+ *     repeated until each site had one chance on average).
+ *   - Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
+ *     numbers: as easy as 1, 2, 3", SC'11), written from that paper's definition.
+ *
+ * Encoding (all arrays row-major, index j*L + i, i = x column, j = y row):
+ *   sx[j*L+i] = 1 if sigma_x(i,j) = h(i+1,j) - h(i,j) = +1, else 0
+ *   sy[j*L+i] = 1 if sigma_y(i,j) = h(i,j+1) - h(i,j) = +1, else 0
+ *
+ * Schedule of one sweep s (one Monte Carlo step, L*L attempts), parameters
+ * (L, Bx, By, seed, sample, Tp, Tq); cells are 4x4 sites, bisected into four
+ * 2x2 quadrant sets; 16 single-hit rounds per sweep:
+ *   key  = (seed & 0xffffffff, seed >> 32)
+ *   ctr  = (tag << 28 | index, c1, s, sample)
+ *   origin:   w = philox(0<<28, 0, s, sample); ox = w0 & (L-1); oy = w1 & (L-1)
+ *   tile (tx,ty), id T = ty*(L/Bx) + tx, anchored at (ox + tx*Bx, oy + ty*By) mod L
+ *   set of round r: k = (philox(1<<28, T, s, sample).w0 >> 2r) & 3, qx = k&1, qy = k>>1
+ *   cell (cx,cy) of the tile, word wx = cx>>5, bit b = cx&31, nwx = ceil(Bx/128):
+ *     P = philox(2<<28 | ((cy*nwx+wx)<<3) | (r>>1), T, s, sample)
+ *     xi = bit b of P[2*(r&1)], yi = bit b of P[2*(r&1)+1]
+ *     u = 4cx + 2qx + xi, v = 4cy + 2qy + yi  (tile-local); dead if u==0 or v==0
+ *     site (i,j) = ((ox + tx*Bx + u) mod L, (oy + ty*By + v) mod L)
+ *   acceptance number of that attempt (16 bits, level 0 = most significant):
+ *     A_m = philox(3<<28 | ((cy*nwx+wx)<<6) | (r<<2) | m, T, s, sample), m = 0..3
+ *     level n uses bit b of A_{n>>2}[n&3];  U = sum_n bit << (15-n)
+ *   a minimum flips iff U < Tp, a maximum flips iff U < Tq,
+ *   Tp = min(65536, floor(p*65536 + 0.5)), likewise Tq.
+ * Random-sequential reference (no decomposition), attempt a of sweep s:
+ *   w = philox(4<<28 | (a>>32), a & 0xffffffff, s, sample)
+ *   site (w0 & (L-1), w1 & (L-1)), U = w2 >> 16.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10 (Salmon et al., SC'11, Sec. 3 and Table 2).                  */
+/* ------------------------------------------------------------------------- */
+static const uint32_t PHILOX_M0 = 0xD2511F53u; /* round multipliers */
+static const uint32_t PHILOX_M1 = 0xCD9E8D57u;
+static const uint32_t PHILOX_W0 = 0x9E3779B9u; /* Weyl key increments */
+static const uint32_t PHILOX_W1 = 0xBB67AE85u;
+
+/* One Philox S-box round on 4 words: two 32x32->64 multiplications, their
+ * high halves XORed with the other two words and the round key. */
+static void philox_round(uint32_t x[4], const uint32_t k[2]) {
+    uint64_t p0 = (uint64_t)PHILOX_M0 * x[0];
+    uint64_t p1 = (uint64_t)PHILOX_M1 * x[2];
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t y0 = hi1 ^ x[1] ^ k[0];
+    uint32_t y1 = lo1;
+    uint32_t y2 = hi0 ^ x[3] ^ k[1];
+    uint32_t y3 = lo0;
+    x[0] = y0; x[1] = y1; x[2] = y2; x[3] = y3;
+}
+
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t x[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+    uint32_t k[2] = {key[0], key[1]};
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k[0] += PHILOX_W0; k[1] += PHILOX_W1; }
+        philox_round(x, k);
+    }
+    out[0] = x[0]; out[1] = x[1]; out[2] = x[2]; out[3] = x[3];
+}
+
+static void philox_at(uint32_t tag_index, uint32_t c1, uint32_t s, uint32_t sample,
+                      uint64_t seed, uint32_t out[4]) {
+    uint32_t ctr[4] = {tag_index, c1, s, sample};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    orc_philox(ctr, key, out);
+}
+
+enum { TAG_ORIGIN = 0, TAG_SET = 1, TAG_POS = 2, TAG_ACC = 3, TAG_RSU = 4 };
+
+/* ------------------------------------------------------------------------- */
+/* Model (Sec. 2.1).                                                          */
+/* ------------------------------------------------------------------------- */
+
+/* Acceptance threshold out of 2^16 for a per-attempt probability (eq. rule). */
+uint32_t orc_threshold(double p) {
+    if (!(p > 0.0)) return 0;           /* also maps NaN to 0 */
+    if (p >= 1.0) return 65536u;
+    double t = p * 65536.0 + 0.5;
+    uint32_t T = (uint32_t)t;           /* floor for t >= 0 */
+    return T > 65536u ? 65536u : T;
+}
+
+/* Flat start: heights h(i,j) = (i+j) & 1, so every slope is +1 where i+j is
+ * even and -1 where it is odd (Sec. 2.1, "flat initial configuration"). */
+void orc_init_flat(uint32_t L, uint8_t* sx, uint8_t* sy) {
+    for (uint32_t j = 0; j < L; ++j)
+        for (uint32_t i = 0; i < L; ++i) {
+            uint8_t up = ((i + j) & 1u) == 0u;
+            sx[(size_t)j * L + i] = up;
+            sy[(size_t)j * L + i] = up;
+        }
+}
+
+/* Eq. (rule) at site (i,j) of the periodic lattice. Reads the two x-slopes
+ * entering and leaving the site and the two y-slopes; the pattern
+ * (-1,+1 ; -1,+1) is a local minimum (all four neighbours are higher), the
+ * pattern (+1,-1 ; +1,-1) a local maximum. A flip negates all four slopes,
+ * which moves h(i,j) by +2 (minimum, if acc_min) or -2 (maximum, if acc_max).
+ * Returns the height change of the site. */
+int orc_attempt(uint32_t L, uint8_t* sx, uint8_t* sy, uint32_t i, uint32_t j,
+                int acc_min, int acc_max) {
+    uint32_t im = (i + L - 1) & (L - 1), jm = (j + L - 1) & (L - 1);
+    size_t here = (size_t)j * L + i, left = (size_t)j * L + im, below = (size_t)jm * L + i;
+    int a = sx[left], b = sx[here], c = sy[below], d = sy[here];
+    int is_min = (a == 0 && b == 1 && c == 0 && d == 1);
+    int is_max = (a == 1 && b == 0 && c == 1 && d == 0);
+    if ((is_min && acc_min) || (is_max && acc_max)) {
+        sx[left] ^= 1; sx[here] ^= 1; sy[below] ^= 1; sy[here] ^= 1;
+        return is_min ? 2 : -2;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Random numbers of the decomposed schedule (header comment).                */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    uint32_t L, Bx, By, Tp, Tq, sample;
+    uint64_t seed;
+} orc_params;
+
+/* One-entry memo of the last Philox block, so that the 32 cells that share a
+ * block do not recompute it; the values are exactly philox_at(...). */
+typedef struct { int valid; uint32_t tag_index, c1, s, sample; uint64_t seed; uint32_t w[4]; } memo;
+
+static const uint32_t* memo_philox(memo* m, uint32_t tag_index, uint32_t c1, uint32_t s,
+                                   uint32_t sample, uint64_t seed) {
+    if (!(m->valid && m->tag_index == tag_index && m->c1 == c1 && m->s == s &&
+          m->sample == sample && m->seed == seed)) {
+        philox_at(tag_index, c1, s, sample, seed, m->w);
+        m->valid = 1; m->tag_index = tag_index; m->c1 = c1; m->s = s;
+        m->sample = sample; m->seed = seed;
+    }
+    return m->w;
+}
+
+static uint32_t words_per_cell_row(uint32_t Bx) { return (Bx / 4 + 31) / 32; }
+
+/* Position bits (xi, yi) of cell (cx,cy) in round r of tile T, sweep s. */
+static void position_bits(const orc_params* P, memo* m, uint32_t T, uint32_t s,
+                          uint32_t cx, uint32_t cy, uint32_t r, uint32_t* xi, uint32_t* yi) {
+    uint32_t nwx = words_per_cell_row(P->Bx);
+    uint32_t row_word = cy * nwx + (cx >> 5);
+    uint32_t idx = ((uint32_t)TAG_POS << 28) | (row_word << 3) | (r >> 1);
+    const uint32_t* w = memo_philox(m, idx, T, s, P->sample, P->seed);
+    uint32_t b = cx & 31u;
+    *xi = (w[2 * (r & 1u)] >> b) & 1u;
+    *yi = (w[2 * (r & 1u) + 1] >> b) & 1u;
+}
+
+/* 16-bit acceptance number of cell (cx,cy) in round r of tile T, sweep s. */
+static uint32_t acceptance_number(const orc_params* P, memo* m4, uint32_t T, uint32_t s,
+                                  uint32_t cx, uint32_t cy, uint32_t r) {
+    uint32_t nwx = words_per_cell_row(P->Bx);
+    uint32_t row_word = cy * nwx + (cx >> 5);
+    uint32_t b = cx & 31u, U = 0;
+    for (uint32_t n = 0; n < 16; ++n) {
+        uint32_t mi = n >> 2;
+        uint32_t idx = ((uint32_t)TAG_ACC << 28) | (row_word << 6) | (r << 2) | mi;
+        const uint32_t* w = memo_philox(&m4[mi], idx, T, s, P->sample, P->seed);
+        U |= ((w[n & 3u] >> b) & 1u) << (15 - n);
+    }
+    return U;
+}
+
+/* A fixed pseudo-random permutation used only to reorder independent work
+ * (tiles, cells) in the order-independence tests; it is not part of the
+ * schedule's randomness. */
+static void shuffle(uint32_t* a, uint32_t n, uint64_t state) {
+    for (uint32_t i = 0; i < n; ++i) a[i] = i;
+    if (state == 0) return;
+    for (uint32_t i = n; i > 1; --i) {
+        state ^= state << 13; state ^= state >> 7; state ^= state << 17;
+        uint32_t jdx = (uint32_t)(state % i);
+        uint32_t t = a[i - 1]; a[i - 1] = a[jdx]; a[jdx] = t;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* One sweep of the decomposed dynamics (Sec. 3 and 3.1).                      */
+/* order: 0 = tiles and cells in natural order, 1 = both reversed, >= 2 = both */
+/* shuffled with a permutation seeded by `order` (result must not change).    */
+/* rounds: number of single-hit rounds to perform (16 = the full sweep; fewer */
+/* only for tests that look inside a sweep). Returns 0, or -1 on bad input.   */
+/* ------------------------------------------------------------------------- */
+int orc_sweep(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32_t Tq,
+              uint64_t seed, uint32_t sample, uint32_t s,
+              uint8_t* sx, uint8_t* sy, int64_t* h00, uint64_t order, uint32_t rounds) {
+    if (rounds > 16) return -1;
+    if (L < 4 || (L & (L - 1)) || Bx < 4 || By < 4 || (Bx & (Bx - 1)) || (By & (By - 1)) ||
+        Bx > L || By > L || Tp > 65536u || Tq > 65536u)
+        return -1;
+    orc_params P = {L, Bx, By, Tp, Tq, sample, seed};
+
+    /* Device layer: the origin of the tile grid moves to a random site each sweep. */
+    uint32_t w[4];
+    philox_at((uint32_t)TAG_ORIGIN << 28, 0, s, sample, seed, w);
+    uint32_t ox = w[0] & (L - 1), oy = w[1] & (L - 1);
+
+    uint32_t ntx = L / Bx, nty = L / By, ntiles = ntx * nty;
+    uint32_t ncx = Bx / 4, ncy = By / 4, ncells = ncx * ncy;
+    uint32_t* tile_order = (uint32_t*)malloc(sizeof(uint32_t) * ntiles);
+    uint32_t* cell_order = (uint32_t*)malloc(sizeof(uint32_t) * ncells);
+    if (!tile_order || !cell_order) { free(tile_order); free(cell_order); return -1; }
+    shuffle(tile_order, ntiles, order >= 2 ? order : 0);
+    if (order == 1)
+        for (uint32_t n = 0; n < ntiles; ++n) tile_order[n] = ntiles - 1 - n;
+
+    memo mpos = {0}, macc[4] = {{0}};
+    for (uint32_t n = 0; n < ntiles; ++n) {
+        uint32_t T = tile_order[n];
+        uint32_t tx = T % ntx, ty = T / ntx;
+        uint32_t x0 = ox + tx * Bx, y0 = oy + ty * By;
+        uint32_t setw[4];
+        philox_at((uint32_t)TAG_SET << 28, T, s, sample, seed, setw);
+
+        /* Work-group layer: 16 single-hit rounds; each picks one of the four
+         * quadrant sets at random (possibly the same as before) and gives every
+         * cell one attempt inside its active quadrant. */
+        for (uint32_t r = 0; r < rounds; ++r) {
+            uint32_t k = (setw[0] >> (2 * r)) & 3u;
+            uint32_t qx = k & 1u, qy = k >> 1;
+            shuffle(cell_order, ncells, order >= 2 ? order * 0x9E3779B97F4A7C15ull + T + 1 : 0);
+            if (order == 1)
+                for (uint32_t c = 0; c < ncells; ++c) cell_order[c] = ncells - 1 - c;
+            for (uint32_t c = 0; c < ncells; ++c) {
+                uint32_t cell = cell_order[c];
+                uint32_t cx = cell % ncx, cy = cell / ncx;
+                uint32_t xi, yi;
+                position_bits(&P, &mpos, T, s, cx, cy, r, &xi, &yi);
+                uint32_t u = 4 * cx + 2 * qx + xi;
+                uint32_t v = 4 * cy + 2 * qy + yi;
+                if (u == 0 || v == 0) continue;          /* dead border of the tile */
+                uint32_t i = (x0 + u) & (L - 1), j = (y0 + v) & (L - 1);
+                uint32_t U = acceptance_number(&P, macc, T, s, cx, cy, r);
+                int dh = orc_attempt(L, sx, sy, i, j, U < Tp, U < Tq);
+                if (dh != 0 && i == 0 && j == 0 && h00) *h00 += dh;
+            }
+        }
+    }
+    free(tile_order);
+    free(cell_order);
+    return 0;
+}
+
+/* n sweeps s = t0 .. t0+n-1 in natural order. */
+int orc_run(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32_t Tq,
+            uint64_t seed, uint32_t sample, uint32_t t0, uint32_t n,
+            uint8_t* sx, uint8_t* sy, int64_t* h00) {
+    for (uint32_t k = 0; k < n; ++k) {
+        int rc = orc_sweep(L, Bx, By, Tp, Tq, seed, sample, t0 + k, sx, sy, h00, 0, 16);
+        if (rc) return rc;
+    }
+    return 0;
+}
+
+/* Random-sequential update: L*L attempts at uniformly random sites per sweep,
+ * no decomposition (the dynamics the decomposition approximates). */
+int orc_rsu_run(uint32_t L, uint32_t Tp, uint32_t Tq, uint64_t seed, uint32_t sample,
+                uint32_t t0, uint32_t n, uint8_t* sx, uint8_t* sy, int64_t* h00) {
+    if (L < 4 || (L & (L - 1)) || Tp > 65536u || Tq > 65536u) return -1;
+    uint64_t N = (uint64_t)L * L;
+    for (uint32_t k = 0; k < n; ++k) {
+        uint32_t s = t0 + k;
+        for (uint64_t a = 0; a < N; ++a) {
+            uint32_t w[4];
+            philox_at(((uint32_t)TAG_RSU << 28) | (uint32_t)(a >> 32), (uint32_t)a, s, sample, seed, w);
+            uint32_t i = w[0] & (L - 1), j = w[1] & (L - 1), U = w[2] >> 16;
+            int dh = orc_attempt(L, sx, sy, i, j, U < Tp, U < Tq);
+            if (dh != 0 && i == 0 && j == 0 && h00) *h00 += dh;
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Heights and width (Sec. 2.1).                                               */
+/* ------------------------------------------------------------------------- */
+
+/* Height reconstruction in the gauge h(0,0) = 0: walk along row 0 to column i,
+ * then up column i to row j:  h(i,j) = sum_{l<i} sigma_x(l,0) + sum_{k<j} sigma_y(i,k). */
+void orc_heights(uint32_t L, const uint8_t* sx, const uint8_t* sy, int64_t* h) {
+    int64_t base = 0;
+    for (uint32_t i = 0; i < L; ++i) {
+        int64_t hh = base;
+        for (uint32_t j = 0; j < L; ++j) {
+            h[(size_t)j * L + i] = hh;
+            hh += sy[(size_t)j * L + i] ? 1 : -1;
+        }
+        base += sx[i] ? 1 : -1;   /* sigma_x(i, 0) */
+    }
+}
+
+/* Exact sums S1 = sum h, S2 = sum h^2 (S2 as two 64-bit halves). */
+void orc_sums(uint32_t L, const int64_t* h, int64_t* S1, uint64_t* S2_lo, uint64_t* S2_hi) {
+    int64_t s1 = 0;
+    unsigned __int128 s2 = 0;
+    uint64_t N = (uint64_t)L * L;
+    for (uint64_t n = 0; n < N; ++n) {
+        s1 += h[n];
+        s2 += (unsigned __int128)((__int128)h[n] * h[n]);
+    }
+    *S1 = s1;
+    *S2_lo = (uint64_t)s2;
+    *S2_hi = (uint64_t)(s2 >> 64);
+}
+
+/* Eq. (Wdef): W^2 = (1/N) sum h^2 - ((1/N) sum h)^2 with N = L^2 sites,
+ * evaluated as (N*S2 - S1^2) / N^2 with the numerator exact in 128 bits. */
+double orc_w2(uint64_t N, int64_t S1, uint64_t S2_lo, uint64_t S2_hi) {
+    unsigned __int128 S2 = ((unsigned __int128)S2_hi << 64) | S2_lo;
+    unsigned __int128 num = (unsigned __int128)N * S2 - (unsigned __int128)((__int128)S1 * S1);
+    return (double)num / ((double)N * (double)N);
+}
+
+/* Canonical packed exchange format: row j occupies L/16 words; site i sits in
+ * word j*(L/16) + i/16 at bits 2(i%16) (sigma_x) and 2(i%16)+1 (sigma_y). */
+void orc_pack(uint32_t L, const uint8_t* sx, const uint8_t* sy, uint32_t* words) {
+    size_t W = (size_t)L * L / 16;
+    memset(words, 0, W * sizeof(uint32_t));
+    for (uint32_t j = 0; j < L; ++j)
+        for (uint32_t i = 0; i < L; ++i) {
+            size_t n = (size_t)j * L + i, wi = (size_t)j * (L / 16) + i / 16;
+            words[wi] |= ((uint32_t)sx[n] << (2 * (i % 16))) | ((uint32_t)sy[n] << (2 * (i % 16) + 1));
+        }
+}
+
+void orc_unpack(uint32_t L, const uint32_t* words, uint8_t* sx, uint8_t* sy) {
+    for (uint32_t j = 0; j < L; ++j)
+        for (uint32_t i = 0; i < L; ++i) {
+            size_t n = (size_t)j * L + i, wi = (size_t)j * (L / 16) + i / 16;
+            sx[n] = (words[wi] >> (2 * (i % 16))) & 1u;
+            sy[n] = (words[wi] >> (2 * (i % 16) + 1)) & 1u;
+        }
+}

@@ -1,0 +1,178 @@
+"""Python handle on the CPU oracle (``kpz_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
+and by the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py``. The
+product package never imports this module.
+
+Arrays follow the oracle's encoding: ``sx``, ``sy`` are ``uint8`` arrays of
+shape ``(L, L)`` indexed ``[j, i]`` (row j = y, column i = x), 1 meaning a
+slope of +1 (Sec. 2.1 of arXiv:1204.5072).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kpz_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libkpz_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc into ``oracle/_build`` and return the path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
+            u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
+            i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+            c = ctypes
+            L.orc_philox.argtypes = [u32p, u32p, u32p]
+            L.orc_threshold.argtypes = [c.c_double]
+            L.orc_threshold.restype = c.c_uint32
+            L.orc_init_flat.argtypes = [c.c_uint32, u8p, u8p]
+            L.orc_attempt.argtypes = [c.c_uint32, u8p, u8p, c.c_uint32, c.c_uint32, c.c_int, c.c_int]
+            L.orc_attempt.restype = c.c_int
+            L.orc_sweep.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32,
+                                    c.c_uint64, c.c_uint32, c.c_uint32, u8p, u8p,
+                                    c.POINTER(c.c_int64), c.c_uint64, c.c_uint32]
+            L.orc_sweep.restype = c.c_int
+            L.orc_run.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32,
+                                  c.c_uint64, c.c_uint32, c.c_uint32, c.c_uint32, u8p, u8p,
+                                  c.POINTER(c.c_int64)]
+            L.orc_run.restype = c.c_int
+            L.orc_rsu_run.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint64, c.c_uint32,
+                                      c.c_uint32, c.c_uint32, u8p, u8p, c.POINTER(c.c_int64)]
+            L.orc_rsu_run.restype = c.c_int
+            L.orc_heights.argtypes = [c.c_uint32, u8p, u8p, i64p]
+            L.orc_sums.argtypes = [c.c_uint32, i64p, c.POINTER(c.c_int64),
+                                   c.POINTER(c.c_uint64), c.POINTER(c.c_uint64)]
+            L.orc_w2.argtypes = [c.c_uint64, c.c_int64, c.c_uint64, c.c_uint64]
+            L.orc_w2.restype = c.c_double
+            L.orc_pack.argtypes = [c.c_uint32, u8p, u8p, u32p]
+            L.orc_unpack.argtypes = [c.c_uint32, u32p, u8p, u8p]
+            _lib = L
+    return _lib
+
+
+# --------------------------------------------------------------------------- #
+def philox(ctr, key) -> np.ndarray:
+    """Philox4x32-10 block for counter ``ctr`` (4 words) and key ``key`` (2 words)."""
+    out = np.zeros(4, np.uint32)
+    lib().orc_philox(np.asarray(ctr, np.uint32), np.asarray(key, np.uint32), out)
+    return out
+
+
+def threshold(p: float) -> int:
+    """Acceptance threshold out of 2^16 used for probability ``p``."""
+    return int(lib().orc_threshold(float(p)))
+
+
+class State:
+    """Lattice state of the oracle: slopes plus the absolute height of (0,0)."""
+
+    def __init__(self, L: int, sx: np.ndarray, sy: np.ndarray, h00: int = 0, t: int = 0):
+        self.L = int(L)
+        self.sx = np.ascontiguousarray(sx, np.uint8)
+        self.sy = np.ascontiguousarray(sy, np.uint8)
+        self.h00 = int(h00)
+        self.t = int(t)
+
+    @classmethod
+    def flat(cls, L: int) -> "State":
+        sx = np.zeros((L, L), np.uint8)
+        sy = np.zeros((L, L), np.uint8)
+        lib().orc_init_flat(L, sx, sy)
+        return cls(L, sx, sy)
+
+    def copy(self) -> "State":
+        return State(self.L, self.sx.copy(), self.sy.copy(), self.h00, self.t)
+
+    # -- dynamics ------------------------------------------------------------
+    def sweep(self, Bx, By, p, q, seed, sample=0, order=0, s=None, rounds=16):
+        s = self.t if s is None else s
+        h = ctypes.c_int64(self.h00)
+        rc = lib().orc_sweep(self.L, Bx, By, threshold(p), threshold(q), seed, sample, s,
+                             self.sx, self.sy, ctypes.byref(h), order, rounds)
+        if rc:
+            raise ValueError("invalid oracle parameters")
+        self.h00 = h.value
+        self.t = s + 1
+        return self
+
+    def run(self, n, Bx, By, p, q, seed, sample=0):
+        h = ctypes.c_int64(self.h00)
+        rc = lib().orc_run(self.L, Bx, By, threshold(p), threshold(q), seed, sample,
+                           self.t, n, self.sx, self.sy, ctypes.byref(h))
+        if rc:
+            raise ValueError("invalid oracle parameters")
+        self.h00 = h.value
+        self.t += n
+        return self
+
+    def rsu(self, n, p, q, seed, sample=0):
+        h = ctypes.c_int64(self.h00)
+        rc = lib().orc_rsu_run(self.L, threshold(p), threshold(q), seed, sample,
+                               self.t, n, self.sx, self.sy, ctypes.byref(h))
+        if rc:
+            raise ValueError("invalid oracle parameters")
+        self.h00 = h.value
+        self.t += n
+        return self
+
+    def attempt(self, i, j, acc_min=True, acc_max=True) -> int:
+        return int(lib().orc_attempt(self.L, self.sx, self.sy, i, j, int(acc_min), int(acc_max)))
+
+    # -- observables ---------------------------------------------------------
+    def heights(self, absolute=False) -> np.ndarray:
+        h = np.zeros((self.L, self.L), np.int64)
+        lib().orc_heights(self.L, self.sx, self.sy, h)
+        return h + self.h00 if absolute else h
+
+    def sums(self):
+        """(S1, S2) of the relative heights (gauge h(0,0) = 0), exact Python ints."""
+        h = self.heights()
+        s1 = ctypes.c_int64()
+        lo = ctypes.c_uint64()
+        hi = ctypes.c_uint64()
+        lib().orc_sums(self.L, h, ctypes.byref(s1), ctypes.byref(lo), ctypes.byref(hi))
+        return s1.value, (hi.value << 64) | lo.value
+
+    def w2(self) -> float:
+        s1, s2 = self.sums()
+        return w2_from_sums(self.L * self.L, s1, s2)
+
+    def packed(self) -> np.ndarray:
+        """Canonical packed words, shape (L*L/16,), requires L >= 16."""
+        w = np.zeros(self.L * self.L // 16, np.uint32)
+        lib().orc_pack(self.L, self.sx, self.sy, w)
+        return w
+
+    @classmethod
+    def from_packed(cls, L: int, words: np.ndarray, h00: int = 0, t: int = 0) -> "State":
+        sx = np.zeros((L, L), np.uint8)
+        sy = np.zeros((L, L), np.uint8)
+        lib().orc_unpack(L, np.ascontiguousarray(words, np.uint32), sx, sy)
+        return cls(L, sx, sy, h00, t)
+
+
+def w2_from_sums(N: int, S1: int, S2: int) -> float:
+    mask = (1 << 64) - 1
+    return float(lib().orc_w2(N, S1, S2 & mask, S2 >> 64))
