@@ -1,0 +1,317 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 octahedron KPZ engine.
+
+Workload (one step): the L = 2^16 job -- flat checkerboard start, p = 1, q = 0,
+2000 Monte Carlo steps (sweeps of L^2 attempts each) with the exact width W^2
+sampled at log-spaced times, through the C ABI of include/kpz.h. Metric:
+site-update attempts per second (Kelling et al., arXiv:1204.5072, Sec. 4
+report updates per second). One JSON line on stdout (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+`--impl reference` times the CPU oracle (the plain single-threaded
+restatement of the same schedule) on a bounded sample of the workload.
+Under torchrun every rank runs its own independent realisation (sample =
+rank): the path has no exchange step, so the scaling is weak and replica-only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import inputs as I  # noqa: E402
+
+METRIC = "KPZ site-update attempts/s at L=2^16 (frac. of roofline); batched realisations/s"
+UNIT = "attempts/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--L", type=int, default=I.L65536_2000.L)
+    ap.add_argument("--mcs", type=int, default=I.L65536_2000.mcs)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample-mcs", type=int, default=100)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------- #
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- #
+def cpu_baseline(L_full: int, mcs_sample: int):
+    """The oracle, as it stands (single-threaded C), on a bounded sample of the
+    workload: L = 1024 with the same schedule parameters, `mcs_sample` sweeps
+    from the flat start and W^2 at the end."""
+    from oracle import oracle as O
+    L = 1024
+    w = I.L65536_2000
+    st = O.State.flat(L)
+    t0 = time.perf_counter()
+    st.run(mcs_sample, w.bx, w.by, w.p, w.q, w.seed, w.sample)
+    st.w2()
+    dt = time.perf_counter() - t0
+    return {"value": mcs_sample * L * L / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"L={L} p={w.p} q={w.q} seed={w.seed}, {mcs_sample} MCS from the flat start "
+                      f"+ W^2, 128x128 tiles (sub-run of the L={L_full} workload)",
+            "seconds": dt}
+
+
+def run_reference(a):
+    """--impl reference: the CPU oracle timed on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    w = I.L65536_2000
+    L, per_step = 1024, 4
+    O.build()
+    st = O.State.flat(L)
+    for _ in range(a.warmup):
+        st.run(per_step, w.bx, w.by, w.p, w.q, w.seed, w.sample)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        st.run(per_step, w.bx, w.by, w.p, w.q, w.seed, w.sample)
+        st.w2()
+    dt = time.perf_counter() - t0
+    value = a.steps * per_step * L * L / dt
+    sample = (f"L={L} p={w.p} q={w.q} seed={w.seed}, {per_step} MCS + W^2 per step, "
+              f"128x128 tiles (sub-run of the L={a.L} workload)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1e3 * dt / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic (flat checkerboard start)",
+            "config": {"workload": f"octahedron KPZ L={a.L} p=1 q=0 {a.mcs} MCS (CPU oracle sample)",
+                       "L": a.L, "mcs": a.mcs},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- #
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1204_5072_gb300 as eng
+    from paper_1204_5072_gb300._lib import launch_count
+
+    w = I.L65536_2000
+    L, mcs = a.L, a.mcs
+    times = I.sample_times(mcs)
+    stream = torch.cuda.current_stream()
+    lat = eng.Lattice(L, w.p, w.q, seed=w.seed, sample=rank)
+
+    sweep_events = []  # (start, end, n_sweeps) on the engine's stream
+
+    def job(record=False):
+        lat.reset()
+        t_prev = 0
+        rough = []
+        for t in times:
+            n = t - t_prev
+            if n:
+                if record:
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                lat.run(n)
+                if record:
+                    e1.record(stream)
+                    sweep_events.append((e0, e1, n))
+            rough.append(lat.roughness())
+            t_prev = t
+        return rough
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(a.warmup, 3)):
+        job()
+    barrier()
+    launches0 = launch_count()
+    with ClockSampler(local) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for _ in range(a.steps):
+            rough = job(record=True)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    launches = launch_count() - launches0
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    if dist:
+        tt = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    attempts = float(world) * a.steps * mcs * L * L
+    value = attempts / elapsed
+    sweep_ms = sum(e0.elapsed_time(e1) for e0, e1, _ in sweep_events)
+    n_sweeps = sum(n for _, _, n in sweep_events)
+    per_sweep_s = sweep_ms / 1e3 / n_sweeps
+
+    # Roofline of the sweep kernel: 2 slope bits read + 2 written per site.
+    alg_bytes = 0.5 * L * L
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / per_sweep_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "sweep_kernel",
+                "alg_bytes_per_launch": alg_bytes, "launch_ms": per_sweep_s * 1e3,
+                "peak_source": f"{peak_kind} hbm_gbs"}
+
+    # End to end through the C ABI with host buffers: upload the start state
+    # from pinned memory, run the job with W^2 sampling, read the final lattice.
+    e2e = None
+    if not a.no_e2e:
+        nwords = L * L // 16
+        host_in = torch.empty(nwords, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+        host_in.reshape(L, L // 16)[0::2] = 0x33333333
+        host_in.reshape(L, L // 16)[1::2] = 0xCCCCCCCC
+        host_out = torch.empty(nwords, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+
+        def e2e_step():
+            lat.set_slopes(host_in, h00=0, t=0)
+            t_prev = 0
+            for t in times:
+                if t - t_prev:
+                    lat.run(t - t_prev)
+                lat.roughness()
+                t_prev = t
+            lat.slopes_into(host_out)
+
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            e2e_step()
+        barrier()
+        e2e_dt = time.perf_counter() - t0
+        if dist:
+            tt = torch.tensor([e2e_dt], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_dt = float(tt.item())
+        e2e = {"value": attempts / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": nwords * 4,
+               "d2h_bytes_per_step": nwords * 4 + len(times) * 48}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        cpu = cpu_baseline(L, a.cpu_sample_mcs)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+                "warmup": max(a.warmup, 3), "ms_per_step": 1e3 * elapsed / a.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+                "data": "synthetic (flat checkerboard start, p=1 q=0)",
+                "config": {"workload": f"octahedron KPZ L={L} p=1 q=0 {mcs} MCS, W^2 at "
+                                       f"{len(times)} log-spaced times, 1 realisation per GPU",
+                           "L": L, "p": w.p, "q": w.q, "mcs": mcs, "samples": len(times),
+                           "tile": "128x128, 4x4 cells", "seed": w.seed,
+                           "l2": "lattice (L^2/4 bytes) larger than L2", "parallelism": f"replicas{world}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clk.summary(), "gpu_launches": launches,
+                "w2_final": rough[-1]["w2"]}
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,140 @@
+/*
+ * kpz.h -- C ABI of the GB300 octahedron KPZ lattice engine.
+ *
+ * Model (Kelling, Odor, Nagy, Schulz, Heinig, arXiv:1204.5072, Sec. 2.1):
+ * an L x L periodic lattice of octahedron slopes sigma_x, sigma_y = +-1; a site
+ * that is a local minimum of its four neighbours is raised by 2 with
+ * probability p, a local maximum is lowered by 2 with probability q
+ * (eq. rule). One Monte Carlo step (MCS) is L*L update attempts. Time is
+ * advanced with the paper's decomposition (Sec. 3, 3.1): a dead-border tile
+ * grid whose origin moves to a random site every sweep, and single-hit double
+ * tiling of each 128 x 128 tile into 4 x 4 cells with four 2 x 2 quadrant sets.
+ * The random numbers are counter-based Philox4x32-10 keyed by
+ * (seed, sample, sweep, tile, cell row, round), so a run is a pure function of
+ * (L, p, q, seed, sample, tile shape, number of sweeps).
+ *
+ * Conventions
+ *   - All functions return kpz_status; no C++ exception crosses this boundary.
+ *   - Host pointers are owned by the caller and only read or written during
+ *     the call. Device memory is owned by the context unless the caller passes
+ *     `dev_buf` in kpz_opts, in which case the caller keeps it alive until
+ *     kpz_free and the library never frees it.
+ *   - Work is queued on the context's stream (kpz_opts.stream, or the legacy
+ *     default stream when NULL). Functions that return data to the host
+ *     synchronise that stream; kpz_run does not.
+ *   - A context is not thread-safe; distinct contexts are independent.
+ *   - After KPZ_ECUDA the context is poisoned: every later call returns
+ *     KPZ_ESTATE until kpz_free.
+ *
+ * Packed exchange format (kpz_slopes / kpz_set_slopes): row j (y) occupies
+ * L/16 consecutive 32-bit words; site i (x) sits in word j*(L/16) + i/16 at bit
+ * 2*(i%16) (sigma_x, 1 = +1) and bit 2*(i%16)+1 (sigma_y). The engine's own
+ * HBM layout is different (bit-sliced per cell row) and is not part of the ABI.
+ */
+#ifndef KPZ_H
+#define KPZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KPZ_OK = 0,
+    KPZ_EINVAL = 1,   /* invalid argument; nothing was launched or changed    */
+    KPZ_ENOMEM = 2,   /* device allocation failed or dev_buf too small        */
+    KPZ_ECUDA = 3,    /* a CUDA call failed; the context is now poisoned      */
+    KPZ_ETIMEOUT = 4, /* a bounded device-side wait gave up                   */
+    KPZ_ESTATE = 5,   /* context poisoned by an earlier error                 */
+    KPZ_ENODEV = 6    /* no usable CUDA device                                */
+} kpz_status;
+
+typedef struct kpz_ctx kpz_ctx;
+
+/* Options; a NULL pointer or zero fields select the defaults. */
+typedef struct {
+    uint32_t bx, by;      /* tile shape in sites; only 128 x 128 is built (0 = 128)  */
+    uint32_t run;         /* tiles one warp sweeps along x per sweep (0 = auto);
+                             execution only, it does not change the result           */
+    uint32_t warps_per_cta; /* 0 = auto; execution only                              */
+    void* stream;         /* cudaStream_t to queue work on (NULL = default stream)  */
+    void* dev_buf;        /* optional caller-owned device memory for the lattice and
+                             its scratch; at least kpz_device_bytes(L) bytes,
+                             256-byte aligned                                        */
+    size_t dev_bytes;     /* size of dev_buf                                        */
+} kpz_opts;
+
+/* Roughness at the current time (eq. Wdef). Heights are taken in the gauge
+ * h(0,0) = 0 (relative heights); W^2 does not depend on the gauge.
+ * S2 = sum_h2_hi * 2^64 + sum_h2_lo, exact.                                  */
+typedef struct {
+    uint64_t t_mcs;       /* sweeps done since kpz_init                          */
+    uint64_t n_sites;     /* L*L                                                 */
+    int64_t sum_h;        /* S1 = sum of relative heights                        */
+    uint64_t sum_h2_lo;   /* S2 = sum of squared relative heights, low 64 bits   */
+    uint64_t sum_h2_hi;   /*   high 64 bits                                      */
+    int64_t h00;          /* absolute height of site (0,0) (0 at the flat start) */
+    double w2;            /* (N*S2 - S1^2) / N^2, numerator exact in 128 bits    */
+} kpz_rough;
+
+/* Device bytes a context of lateral size L needs (lattice + scratch), or 0 if
+ * L is not a valid size. */
+size_t kpz_device_bytes(uint32_t L);
+
+/* Create a lattice and set it to the flat start (Sec. 2.1): heights
+ * h(i,j) = (i+j) & 1, so W^2 = 1/4. `init` must be 0 (flat start).
+ * Preconditions (KPZ_EINVAL otherwise, checked before any allocation):
+ *   L a power of two with 128 <= L <= 131072; 0 <= p, q <= 1 (no NaN);
+ *   bx = by = 128 (or 0). p and q are quantised to multiples of 2^-16
+ *   (T = min(65536, floor(x*65536 + 0.5))): attempts accept with U < T for a
+ *   uniform 16-bit U. `sample` is the realisation index that enters the
+ *   Philox counter next to the seed.                                          */
+kpz_status kpz_init(kpz_ctx** out, uint32_t L, double p, double q, uint64_t seed,
+                    uint32_t sample, int init, const kpz_opts* opts);
+
+/* Return the lattice to the flat start (Sec. 2.1) with t = 0 and h(0,0) = 0,
+ * keeping L, p, q, seed, sample and the device memory. Queued on the stream. */
+kpz_status kpz_reset(kpz_ctx* ctx);
+
+/* Queue n_mcs sweeps (n_mcs * L*L attempts) on the context's stream and
+ * return; errors of the queued work surface at the next synchronising call. */
+kpz_status kpz_run(kpz_ctx* ctx, uint64_t n_mcs);
+
+/* Exact height sums and W^2 at the current time (eq. Wdef, Sec. 2.1).
+ * Synchronises the stream. */
+kpz_status kpz_roughness(kpz_ctx* ctx, kpz_rough* out);
+
+/* Heights of all sites into host_out[j*L + i] (caller owns L*L int64).
+ * absolute = 0: gauge h(0,0) = 0; absolute != 0: the absolute heights, i.e.
+ * the relative ones plus the tracked height of site (0,0). Synchronises.     */
+kpz_status kpz_heights(kpz_ctx* ctx, int64_t* host_out, int absolute);
+
+/* Slopes in the packed exchange format into host_out (caller owns L*L/16
+ * uint32). Synchronises. */
+kpz_status kpz_slopes(kpz_ctx* ctx, uint32_t* host_out);
+
+/* Replace the lattice by host_in (packed exchange format, L*L/16 words, a
+ * valid surface: every row of sigma_x and every column of sigma_y sums to
+ * zero), set the absolute height of site (0,0) to h00 and the sweep counter
+ * to t_mcs. Validity is the caller's responsibility. Synchronises.          */
+kpz_status kpz_set_slopes(kpz_ctx* ctx, const uint32_t* host_in, int64_t h00, uint64_t t_mcs);
+
+/* Device pointer of the lattice and its size in bytes (for callers that keep
+ * the lattice resident and time kernels on the context stream). */
+kpz_status kpz_device_lattice(kpz_ctx* ctx, void** dev_ptr, size_t* bytes);
+
+/* Number of kernels this library has launched in the process so far (all
+ * contexts); lets a caller count the GPU work inside a timed region. */
+uint64_t kpz_launch_count(void);
+
+void kpz_free(kpz_ctx* ctx);
+const char* kpz_strerror(kpz_status st);
+/* Last error message of the context (empty string if none). */
+const char* kpz_last_error(const kpz_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KPZ_H */

@@ -1,0 +1,200 @@
+"""ctypes binding of ``libkpz.so`` (include/kpz.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels. PyTorch, when present,
+only supplies device memory and the stream the work is queued on.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+KPZ_OK, KPZ_EINVAL, KPZ_ENOMEM, KPZ_ECUDA, KPZ_ETIMEOUT, KPZ_ESTATE, KPZ_ENODEV = range(7)
+
+
+class KpzError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+class kpz_opts(ctypes.Structure):
+    _fields_ = [("bx", ctypes.c_uint32), ("by", ctypes.c_uint32), ("run", ctypes.c_uint32),
+                ("warps_per_cta", ctypes.c_uint32), ("stream", ctypes.c_void_p),
+                ("dev_buf", ctypes.c_void_p), ("dev_bytes", ctypes.c_size_t)]
+
+
+class kpz_rough(ctypes.Structure):
+    _fields_ = [("t_mcs", ctypes.c_uint64), ("n_sites", ctypes.c_uint64), ("sum_h", ctypes.c_int64),
+                ("sum_h2_lo", ctypes.c_uint64), ("sum_h2_hi", ctypes.c_uint64),
+                ("h00", ctypes.c_int64), ("w2", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load the in-tree engine; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    so = path or _build.SO
+    if not os.path.exists(so):
+        raise ImportError(f"CUDA engine not built: {so} missing (run __graft_entry__.build())")
+    L = ctypes.CDLL(so)
+    c = ctypes
+    vp = c.c_void_p
+    L.kpz_device_bytes.argtypes = [c.c_uint32]
+    L.kpz_device_bytes.restype = c.c_size_t
+    L.kpz_init.argtypes = [c.POINTER(vp), c.c_uint32, c.c_double, c.c_double, c.c_uint64,
+                           c.c_uint32, c.c_int, c.POINTER(kpz_opts)]
+    L.kpz_run.argtypes = [vp, c.c_uint64]
+    L.kpz_reset.argtypes = [vp]
+    L.kpz_roughness.argtypes = [vp, c.POINTER(kpz_rough)]
+    L.kpz_heights.argtypes = [vp, vp, c.c_int]
+    L.kpz_slopes.argtypes = [vp, vp]
+    L.kpz_set_slopes.argtypes = [vp, vp, c.c_int64, c.c_uint64]
+    L.kpz_device_lattice.argtypes = [vp, c.POINTER(vp), c.POINTER(c.c_size_t)]
+    L.kpz_launch_count.argtypes = []
+    L.kpz_launch_count.restype = c.c_uint64
+    L.kpz_free.argtypes = [vp]
+    L.kpz_free.restype = None
+    L.kpz_strerror.argtypes = [c.c_int]
+    L.kpz_strerror.restype = c.c_char_p
+    L.kpz_last_error.argtypes = [vp]
+    L.kpz_last_error.restype = c.c_char_p
+    for fn in ("kpz_init", "kpz_reset", "kpz_run", "kpz_roughness", "kpz_heights", "kpz_slopes",
+               "kpz_set_slopes", "kpz_device_lattice"):
+        getattr(L, fn).restype = c.c_int
+    _lib = L
+    return L
+
+
+def check(st: int, ctx=None):
+    if st != KPZ_OK:
+        lib = load()
+        msg = lib.kpz_strerror(st).decode()
+        if ctx:
+            detail = lib.kpz_last_error(ctx).decode()
+            if detail:
+                msg += ": " + detail
+        raise KpzError(st, msg)
+
+
+def launch_count() -> int:
+    """Kernels launched by the engine in this process so far."""
+    return int(load().kpz_launch_count())
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Lattice:
+    """One L x L octahedron lattice on the GPU (flat start), driven through the C ABI.
+
+    ``stream``: a CUDA stream handle (int) or None for torch's current stream
+    when torch is available, else the default stream. ``device_buffer``: a
+    torch CUDA tensor of at least ``kpz_device_bytes(L)`` bytes to hold the
+    lattice (the caller keeps it alive); None lets the library allocate.
+    """
+
+    def __init__(self, L: int, p: float = 1.0, q: float = 0.0, seed: int = 1, sample: int = 0,
+                 run: int = 0, warps_per_cta: int = 0, stream=None, device_buffer=None):
+        lib = load()
+        self.L, self.p, self.q, self.seed, self.sample = int(L), float(p), float(q), int(seed), int(sample)
+        o = kpz_opts()
+        o.run, o.warps_per_cta = run, warps_per_cta
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream().cuda_stream
+            except ImportError:
+                pass
+        o.stream = stream or None
+        self._buf = device_buffer
+        if device_buffer is not None:
+            o.dev_buf = device_buffer.data_ptr()
+            o.dev_bytes = device_buffer.numel() * device_buffer.element_size()
+        self._ctx = ctypes.c_void_p()
+        st = lib.kpz_init(ctypes.byref(self._ctx), self.L, self.p, self.q, self.seed, self.sample, 0,
+                          ctypes.byref(o))
+        if st != KPZ_OK:
+            ctx = self._ctx
+            self._ctx = None
+            try:
+                check(st, ctx)
+            finally:
+                if ctx:
+                    lib.kpz_free(ctx)
+
+    @staticmethod
+    def device_bytes(L: int) -> int:
+        return int(load().kpz_device_bytes(L))
+
+    def reset(self) -> "Lattice":
+        check(load().kpz_reset(self._ctx), self._ctx)
+        return self
+
+    @property
+    def handle(self):
+        return self._ctx
+
+    def run(self, n_mcs: int) -> "Lattice":
+        check(load().kpz_run(self._ctx, int(n_mcs)), self._ctx)
+        return self
+
+    def roughness(self) -> dict:
+        r = kpz_rough()
+        check(load().kpz_roughness(self._ctx, ctypes.byref(r)), self._ctx)
+        return {"t": r.t_mcs, "n": r.n_sites, "S1": r.sum_h, "S2": (r.sum_h2_hi << 64) | r.sum_h2_lo,
+                "h00": r.h00, "w2": r.w2}
+
+    def heights(self, absolute: bool = False) -> np.ndarray:
+        out = np.empty((self.L, self.L), np.int64)
+        check(load().kpz_heights(self._ctx, _ptr(out), int(bool(absolute))), self._ctx)
+        return out
+
+    def slopes(self) -> np.ndarray:
+        out = np.empty(self.L * self.L // 16, np.uint32)
+        check(load().kpz_slopes(self._ctx, _ptr(out)), self._ctx)
+        return out
+
+    def slopes_into(self, out: np.ndarray) -> np.ndarray:
+        """Packed slopes into a caller-provided uint32 buffer of L*L/16 words."""
+        assert out.dtype == np.uint32 and out.size == self.L * self.L // 16 and out.flags.c_contiguous
+        check(load().kpz_slopes(self._ctx, _ptr(out)), self._ctx)
+        return out
+
+    def set_slopes(self, words: np.ndarray, h00: int = 0, t: int = 0) -> "Lattice":
+        w = np.ascontiguousarray(words, np.uint32)
+        assert w.size == self.L * self.L // 16
+        check(load().kpz_set_slopes(self._ctx, _ptr(w), int(h00), int(t)), self._ctx)
+        return self
+
+    def device_lattice(self):
+        p = ctypes.c_void_p()
+        n = ctypes.c_size_t()
+        check(load().kpz_device_lattice(self._ctx, ctypes.byref(p), ctypes.byref(n)), self._ctx)
+        return p.value, n.value
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            load().kpz_free(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,346 @@
+// kpz_api.cu -- the C ABI declared in include/kpz.h: argument checks, device
+// memory, stream handling and the host side of each call. All lattice
+// arithmetic runs in the kernels of kpz_sweep.cu and kpz_observe.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <atomic>
+#include <new>
+#include <string>
+
+#include "../../include/kpz.h"
+#include "kpz_internal.h"
+
+using namespace kpz;
+
+namespace kpz {
+static std::atomic<uint64_t> g_launches{0};
+void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace kpz
+
+struct kpz_ctx {
+  Geometry g{};
+  uint32_t Tp = 0, Tq = 0, nlev = 0, sample = 0;
+  uint64_t seed = 0;
+  uint32_t run = 1, wpc = 8;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_buf = false;
+  void* buf = nullptr;
+  size_t buf_bytes = 0;
+  uint32_t* lat = nullptr;             // L*L/16 words
+  uint64_t* t_dev = nullptr;           // sweep counter
+  unsigned long long* h00 = nullptr;   // absolute height of site (0,0)
+  unsigned long long* acc = nullptr;   // S1, S2 lo, S2 hi
+  int32_t* col0 = nullptr;             // h(0,j)
+  void* io = nullptr;                  // staging band for host transfers
+  size_t io_bytes = 0;
+  uint64_t t_host = 0;
+  bool poisoned = false;
+  std::string err;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr size_t kIoMax = size_t(64) << 20;
+
+size_t align_up(size_t n) { return (n + kAlign - 1) / kAlign * kAlign; }
+
+bool valid_L(uint32_t L) { return L >= 128u && L <= 131072u && (L & (L - 1u)) == 0u; }
+
+struct Layout {
+  size_t lat, small, col0, io, total;
+};
+
+Layout layout(uint32_t L) {
+  Layout y{};
+  const size_t lat_bytes = (size_t)L * L / 4;   // 2 bits per site
+  y.lat = 0;
+  y.small = align_up(lat_bytes);                 // t, h00, acc[3]
+  y.col0 = y.small + kAlign;
+  y.io = y.col0 + align_up((size_t)L * 4);
+  const size_t io_bytes = std::min(kIoMax, (size_t)L * L * 8);
+  y.total = y.io + align_up(io_bytes);
+  return y;
+}
+
+uint32_t threshold(double p) {
+  if (!(p > 0.0)) return 0u;
+  if (p >= 1.0) return 65536u;
+  const double t = std::floor(p * 65536.0 + 0.5);
+  return t >= 65536.0 ? 65536u : (uint32_t)t;
+}
+
+uint32_t levels(uint32_t Tp, uint32_t Tq) {
+  const uint32_t low = (Tp & 0xFFFFu) | (Tq & 0xFFFFu);
+  if (!low) return 0u;
+  return 16u - (uint32_t)__builtin_ctz(low);
+}
+
+kpz_status fail(kpz_ctx* c, kpz_status st, const std::string& msg) {
+  if (c) {
+    c->err = msg;
+    if (st == KPZ_ECUDA || st == KPZ_ETIMEOUT) c->poisoned = true;
+  }
+  return st;
+}
+
+kpz_status cuda_fail(kpz_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, KPZ_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define KPZ_CUDA(call)                                          \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);    \
+  } while (0)
+
+kpz_status enter(kpz_ctx* ctx) {
+  if (!ctx) return KPZ_EINVAL;
+  if (ctx->poisoned) return KPZ_ESTATE;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  return KPZ_OK;
+}
+
+SweepParams sweep_params(const kpz_ctx* c) {
+  SweepParams P{};
+  P.lat = c->lat;
+  P.t_dev = c->t_dev;
+  P.g = c->g;
+  P.ntx = c->g.L / kTile;
+  P.nty = c->g.L / kTile;
+  P.run = c->run;
+  P.runs_x = P.ntx / c->run;
+  P.Tp = c->Tp;
+  P.Tq = c->Tq;
+  P.nlev = c->nlev;
+  P.k0 = (uint32_t)(c->seed & 0xffffffffu);
+  P.k1 = (uint32_t)(c->seed >> 32);
+  P.sample = c->sample;
+  P.h00 = c->h00;
+  return P;
+}
+
+uint32_t auto_run(uint32_t L) {
+  const uint32_t ntx = L / kTile;
+  const uint64_t tiles = (uint64_t)ntx * ntx;
+  const uint64_t target = 152ull * 16ull * 4ull;  // warps that keep every SM busy
+  uint32_t run = 1;
+  while (run * 2 <= ntx && tiles / (run * 2) >= target && run < 16) run *= 2;
+  return run;
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t kpz_launch_count(void) { return kpz::g_launches.load(std::memory_order_relaxed); }
+
+size_t kpz_device_bytes(uint32_t L) { return valid_L(L) ? layout(L).total : 0; }
+
+const char* kpz_strerror(kpz_status st) {
+  switch (st) {
+    case KPZ_OK: return "ok";
+    case KPZ_EINVAL: return "invalid argument";
+    case KPZ_ENOMEM: return "out of device memory";
+    case KPZ_ECUDA: return "CUDA error";
+    case KPZ_ETIMEOUT: return "device wait timed out";
+    case KPZ_ESTATE: return "context poisoned by an earlier error";
+    case KPZ_ENODEV: return "no CUDA device";
+  }
+  return "unknown status";
+}
+
+const char* kpz_last_error(const kpz_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+kpz_status kpz_init(kpz_ctx** out, uint32_t L, double p, double q, uint64_t seed, uint32_t sample,
+                    int init, const kpz_opts* opts) {
+  if (!out) return KPZ_EINVAL;
+  *out = nullptr;
+  if (!valid_L(L) || std::isnan(p) || std::isnan(q) || p < 0.0 || p > 1.0 || q < 0.0 || q > 1.0 ||
+      init != 0)
+    return KPZ_EINVAL;
+  kpz_opts o{};
+  if (opts) o = *opts;
+  if ((o.bx != 0 && o.bx != kTile) || (o.by != 0 && o.by != kTile)) return KPZ_EINVAL;
+  const uint32_t ntx = L / kTile;
+  if (o.run != 0 && ((o.run & (o.run - 1)) != 0 || o.run > ntx)) return KPZ_EINVAL;
+  if (o.warps_per_cta > 8) return KPZ_EINVAL;
+  const Layout y = layout(L);
+  if (o.dev_buf && (o.dev_bytes < y.total || ((uintptr_t)o.dev_buf % kAlign) != 0)) return KPZ_EINVAL;
+
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return KPZ_ENODEV;
+
+  kpz_ctx* ctx = new (std::nothrow) kpz_ctx();
+  if (!ctx) return KPZ_ENOMEM;
+  cudaGetDevice(&ctx->device);
+  ctx->g.L = L;
+  ctx->g.NR = L / 4;
+  ctx->g.NB = L / 128;
+  ctx->Tp = threshold(p);
+  ctx->Tq = threshold(q);
+  ctx->nlev = levels(ctx->Tp, ctx->Tq);
+  ctx->seed = seed;
+  ctx->sample = sample;
+  ctx->run = o.run ? o.run : auto_run(L);
+  ctx->wpc = o.warps_per_cta ? o.warps_per_cta : 8u;
+  ctx->stream = (cudaStream_t)o.stream;
+  if (o.dev_buf) {
+    ctx->buf = o.dev_buf;
+    ctx->buf_bytes = o.dev_bytes;
+  } else {
+    cudaError_t e = cudaMalloc(&ctx->buf, y.total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete ctx;
+      return KPZ_ENOMEM;
+    }
+    ctx->own_buf = true;
+    ctx->buf_bytes = y.total;
+  }
+  char* base = (char*)ctx->buf;
+  ctx->lat = (uint32_t*)(base + y.lat);
+  ctx->t_dev = (uint64_t*)(base + y.small);
+  ctx->h00 = (unsigned long long*)(base + y.small + 8);
+  ctx->acc = (unsigned long long*)(base + y.small + 16);
+  ctx->col0 = (int32_t*)(base + y.col0);
+  ctx->io = base + y.io;
+  ctx->io_bytes = y.total - y.io;
+
+  kpz_status st = KPZ_OK;
+  cudaError_t e = cudaMemsetAsync(base + y.small, 0, kAlign, ctx->stream);
+  if (e == cudaSuccess) e = launch_init_flat(ctx->lat, ctx->g, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) st = cuda_fail(ctx, e, "kpz_init");
+  *out = ctx;
+  return st;
+}
+
+kpz_status kpz_reset(kpz_ctx* ctx) {
+  kpz_status st = enter(ctx);
+  if (st) return st;
+  KPZ_CUDA(cudaMemsetAsync(ctx->t_dev, 0, 2 * sizeof(uint64_t), ctx->stream));
+  KPZ_CUDA(launch_init_flat(ctx->lat, ctx->g, ctx->stream));
+  ctx->t_host = 0;
+  return KPZ_OK;
+}
+
+kpz_status kpz_run(kpz_ctx* ctx, uint64_t n_mcs) {
+  kpz_status st = enter(ctx);
+  if (st) return st;
+  SweepParams P = sweep_params(ctx);
+  while (n_mcs > 0) {
+    const uint32_t chunk = (uint32_t)std::min<uint64_t>(n_mcs, 1u << 20);
+    for (uint32_t i = 0; i < chunk; ++i) {
+      P.s_add = i;
+      KPZ_CUDA(launch_sweep(P, ctx->wpc, ctx->stream));
+    }
+    KPZ_CUDA(launch_advance(ctx->t_dev, chunk, ctx->stream));
+    ctx->t_host += chunk;
+    n_mcs -= chunk;
+  }
+  return KPZ_OK;
+}
+
+kpz_status kpz_roughness(kpz_ctx* ctx, kpz_rough* out) {
+  kpz_status st = enter(ctx);
+  if (st) return st;
+  if (!out) return fail(ctx, KPZ_EINVAL, "null output");
+  KPZ_CUDA(launch_roughness(ctx->lat, ctx->g, ctx->col0, ctx->acc, ctx->stream));
+  unsigned long long host[4];
+  KPZ_CUDA(cudaMemcpyAsync(host, ctx->acc, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+  KPZ_CUDA(cudaMemcpyAsync(host + 3, ctx->h00, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+  KPZ_CUDA(cudaStreamSynchronize(ctx->stream));
+  const uint64_t N = (uint64_t)ctx->g.L * ctx->g.L;
+  out->t_mcs = ctx->t_host;
+  out->n_sites = N;
+  out->sum_h = (int64_t)host[0];
+  out->sum_h2_lo = host[1];
+  out->sum_h2_hi = host[2];
+  out->h00 = (int64_t)host[3];
+  const unsigned __int128 S2 = ((unsigned __int128)host[2] << 64) | host[1];
+  const __int128 S1 = (int64_t)host[0];
+  const unsigned __int128 num = (unsigned __int128)N * S2 - (unsigned __int128)(S1 * S1);
+  out->w2 = (double)num / ((double)N * (double)N);
+  return KPZ_OK;
+}
+
+kpz_status kpz_heights(kpz_ctx* ctx, int64_t* host_out, int absolute) {
+  kpz_status st = enter(ctx);
+  if (st) return st;
+  if (!host_out) return fail(ctx, KPZ_EINVAL, "null output");
+  const uint32_t L = ctx->g.L;
+  KPZ_CUDA(launch_col0(ctx->lat, ctx->g, ctx->col0, ctx->stream));
+  const uint32_t band = (uint32_t)std::max<size_t>(1, std::min<size_t>(L, ctx->io_bytes / ((size_t)L * 8)));
+  for (uint32_t j0 = 0; j0 < L; j0 += band) {
+    const uint32_t nr = std::min(band, L - j0);
+    KPZ_CUDA(launch_heights(ctx->lat, ctx->g, ctx->col0, j0, nr, absolute ? ctx->h00 : nullptr,
+                            (int64_t*)ctx->io, ctx->stream));
+    KPZ_CUDA(cudaMemcpyAsync(host_out + (size_t)j0 * L, ctx->io, (size_t)nr * L * 8,
+                             cudaMemcpyDeviceToHost, ctx->stream));
+    KPZ_CUDA(cudaStreamSynchronize(ctx->stream));
+  }
+  return KPZ_OK;
+}
+
+kpz_status kpz_slopes(kpz_ctx* ctx, uint32_t* host_out) {
+  kpz_status st = enter(ctx);
+  if (st) return st;
+  if (!host_out) return fail(ctx, KPZ_EINVAL, "null output");
+  const uint32_t L = ctx->g.L;
+  const size_t row_bytes = (size_t)L / 16 * 4;
+  const uint32_t band = (uint32_t)std::min<size_t>(L, ctx->io_bytes / row_bytes) & ~3u;
+  for (uint32_t j0 = 0; j0 < L; j0 += band) {
+    const uint32_t nr = std::min(band, L - j0);
+    KPZ_CUDA(launch_export_packed(ctx->lat, ctx->g, j0, nr, (uint32_t*)ctx->io, ctx->stream));
+    KPZ_CUDA(cudaMemcpyAsync((char*)host_out + (size_t)j0 * row_bytes, ctx->io, nr * row_bytes,
+                             cudaMemcpyDeviceToHost, ctx->stream));
+    KPZ_CUDA(cudaStreamSynchronize(ctx->stream));
+  }
+  return KPZ_OK;
+}
+
+kpz_status kpz_set_slopes(kpz_ctx* ctx, const uint32_t* host_in, int64_t h00, uint64_t t_mcs) {
+  kpz_status st = enter(ctx);
+  if (st) return st;
+  if (!host_in) return fail(ctx, KPZ_EINVAL, "null input");
+  const uint32_t L = ctx->g.L;
+  const size_t row_bytes = (size_t)L / 16 * 4;
+  const uint32_t band = (uint32_t)std::min<size_t>(L, ctx->io_bytes / row_bytes) & ~3u;
+  for (uint32_t j0 = 0; j0 < L; j0 += band) {
+    const uint32_t nr = std::min(band, L - j0);
+    KPZ_CUDA(cudaMemcpyAsync(ctx->io, (const char*)host_in + (size_t)j0 * row_bytes, nr * row_bytes,
+                             cudaMemcpyHostToDevice, ctx->stream));
+    KPZ_CUDA(launch_import_packed(ctx->lat, ctx->g, j0, nr, (const uint32_t*)ctx->io, ctx->stream));
+    KPZ_CUDA(cudaStreamSynchronize(ctx->stream));
+  }
+  unsigned long long small[2] = {(unsigned long long)t_mcs, (unsigned long long)h00};
+  KPZ_CUDA(cudaMemcpyAsync(ctx->t_dev, small, sizeof(small), cudaMemcpyHostToDevice, ctx->stream));
+  KPZ_CUDA(cudaStreamSynchronize(ctx->stream));
+  ctx->t_host = t_mcs;
+  return KPZ_OK;
+}
+
+kpz_status kpz_device_lattice(kpz_ctx* ctx, void** dev_ptr, size_t* bytes) {
+  if (!ctx || !dev_ptr || !bytes) return KPZ_EINVAL;
+  *dev_ptr = ctx->lat;
+  *bytes = (size_t)ctx->g.L * ctx->g.L / 4;
+  return KPZ_OK;
+}
+
+void kpz_free(kpz_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->own_buf && ctx->buf) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->buf);
+  }
+  delete ctx;
+}
+
+}  // extern "C"

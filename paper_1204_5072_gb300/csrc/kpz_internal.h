@@ -1,0 +1,53 @@
+// kpz_internal.h -- launch interfaces between the C-ABI layer and the kernels.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "kpz_common.cuh"
+
+namespace kpz {
+
+// Process-wide count of kernel launches issued by this library.
+void count_launch(uint64_t n = 1);
+
+// One sweep (one MCS) of the decomposed dynamics, Sec. 3 and 3.1.
+struct SweepParams {
+  uint32_t* lat;            // lattice words (layout in kpz_common.cuh)
+  const uint64_t* t_dev;    // device sweep counter; this launch does sweep *t_dev + s_add
+  uint32_t s_add;
+  Geometry g;
+  uint32_t ntx, nty;        // tiles per row / per column of the tile grid
+  uint32_t run;             // tiles one warp processes along x
+  uint32_t runs_x;          // ntx / run
+  uint32_t Tp, Tq;          // acceptance thresholds out of 2^16 (65536 = always)
+  uint32_t nlev;            // acceptance levels that can change a decision
+  uint32_t k0, k1;          // Philox key = seed
+  uint32_t sample;          // realisation index (Philox counter word 3)
+  unsigned long long* h00;  // absolute height of site (0,0), two's complement
+};
+
+cudaError_t launch_sweep(const SweepParams& P, uint32_t warps_per_cta, cudaStream_t st);
+cudaError_t launch_advance(uint64_t* t_dev, uint32_t n, cudaStream_t st);
+
+// Observables and conversions (kpz_observe.cu).
+cudaError_t launch_init_flat(uint32_t* lat, Geometry g, cudaStream_t st);
+// Packed exchange format, rows [j0, j0 + nrows) <-> packed[(j - j0) * L/16 + i/16];
+// for the import j0 and nrows are multiples of 4.
+cudaError_t launch_export_packed(const uint32_t* lat, Geometry g, uint32_t j0, uint32_t nrows,
+                                 uint32_t* packed, cudaStream_t st);
+cudaError_t launch_import_packed(uint32_t* lat, Geometry g, uint32_t j0, uint32_t nrows,
+                                 const uint32_t* packed, cudaStream_t st);
+
+// Exact height sums, eq. Wdef: col0[L] (int32) and acc[3] (S1, S2 lo, S2 hi)
+// are scratch that the caller provides.
+cudaError_t launch_roughness(const uint32_t* lat, Geometry g, int32_t* col0,
+                             unsigned long long* acc, cudaStream_t st);
+// Heights of rows [j0, j0 + nrows) into out[(j - j0) * L + i], gauge h(0,0) = 0
+// plus *h00 when h00 is not null; needs col0 filled by launch_col0.
+cudaError_t launch_col0(const uint32_t* lat, Geometry g, int32_t* col0, cudaStream_t st);
+cudaError_t launch_heights(const uint32_t* lat, Geometry g, const int32_t* col0, uint32_t j0,
+                           uint32_t nrows, const unsigned long long* h00, int64_t* out,
+                           cudaStream_t st);
+
+}  // namespace kpz

@@ -1,0 +1,149 @@
+"""Bit-exact parity of the CUDA engine with the CPU oracle, through the C ABI.
+
+The engine and the oracle implement the same decomposed schedule
+(arXiv:1204.5072, Sec. 3, 3.1; update rule eq. rule, Sec. 2.1) independently;
+integer state must agree bit for bit: the packed slopes, the exact height
+sums S1 and S2 of eq. (Wdef), and the tracked height of site (0,0).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from synth import inputs as I
+from tests.gpu_util import engine
+
+pytestmark = pytest.mark.gpu
+TILE = 128
+
+
+@pytest.fixture(scope="module")
+def eng():
+    return engine()
+
+
+def _same(lat, st, where=""):
+    got = lat.slopes()
+    want = st.packed()
+    if not np.array_equal(got, want):
+        bad = np.flatnonzero(got != want)
+        L = st.L
+        j, wi = divmod(int(bad[0]), L // 16)
+        raise AssertionError(f"{where}: {bad.size} packed words differ, first at row {j} word {wi}")
+    r = lat.roughness()
+    s1, s2 = st.sums()
+    assert (r["S1"], r["S2"]) == (s1, s2), where
+    assert r["h00"] == st.h00, where
+    assert r["w2"] == st.w2(), where
+    assert r["t"] == st.t, where
+
+
+def test_flat_start(eng):
+    for L in (128, 256, 1024):
+        lat = eng.Lattice(L)
+        st = O.State.flat(L)
+        _same(lat, st, f"L={L}")
+        r = lat.roughness()
+        assert r["S1"] == L * L // 2 and r["S2"] == L * L // 2 and r["w2"] == 0.25
+
+
+def test_import_export_heights(eng):
+    states = [O.State(256, *I.separable_surface(256, 3)),
+              O.State.flat(256).run(15, TILE, TILE, 0.8, 0.3, seed=9),
+              O.State.flat(512).run(6, 64, 32, 1.0, 0.0, seed=2)]
+    for k, st in enumerate(states):
+        st.h00 = 10 * k - 7
+        lat = eng.Lattice(st.L)
+        lat.set_slopes(st.packed(), h00=st.h00, t=st.t)
+        assert np.array_equal(lat.slopes(), st.packed())
+        assert np.array_equal(lat.heights(), st.heights())
+        assert np.array_equal(lat.heights(absolute=True), st.heights(absolute=True))
+        r = lat.roughness()
+        assert (r["S1"], r["S2"], r["h00"]) == (*st.sums(), st.h00)
+
+
+CASES = [
+    (128, 1.0, 0.0, 1, 0, 6),       # one tile: the run wraps onto itself
+    (256, 1.0, 0.0, 1, 0, 8),
+    (256, 0.95, 0.05, 1, 0, 6),
+    (512, 0.6, 0.3, 77, 5, 5),
+    (256, 0.5, 0.5, 3, 1, 5),       # lambda = 0
+    (256, 1.0, 1.0, 4, 0, 4),       # both thresholds 2^16: no acceptance draws
+    (256, 0.0, 1.0, 5, 2, 4),
+    (256, 0.3, 0.0, 6, 0, 4),
+    (256, 0.0, 0.0, 7, 0, 3),       # nothing may flip
+    (1024, 1.0, 0.0, (1 << 40) + 3, 9, 4),
+]
+
+
+@pytest.mark.parametrize("L,p,q,seed,sample,n", CASES)
+def test_sweeps_bit_exact(eng, L, p, q, seed, sample, n):
+    lat = eng.Lattice(L, p, q, seed=seed, sample=sample)
+    st = O.State.flat(L)
+    for k in range(n):
+        lat.run(1)
+        st.sweep(TILE, TILE, p, q, seed, sample)
+        _same(lat, st, f"L={L} p={p} q={q} after sweep {k + 1}")
+
+
+def test_L256_1000mcs_every_checkpoint(eng):
+    w = I.L256_1000
+    lat = eng.Lattice(w.L, w.p, w.q, seed=w.seed, sample=w.sample)
+    st = O.State.flat(w.L)
+    for t in I.sample_times(w.mcs):
+        n = t - st.t
+        if n:
+            lat.run(n)
+            st.run(n, w.bx, w.by, w.p, w.q, w.seed, w.sample)
+        _same(lat, st, f"t={t}")
+
+
+def test_L1024_subrun(eng):
+    lat = eng.Lattice(1024, 1.0, 0.0, seed=1)
+    st = O.State.flat(1024)
+    for n in (1, 4, 15):
+        lat.run(n)
+        st.run(n, TILE, TILE, 1.0, 0.0, 1, 0)
+        _same(lat, st, f"t={st.t}")
+
+
+def test_L4096_general_rates(eng):
+    lat = eng.Lattice(4096, 0.95, 0.05, seed=1)
+    st = O.State.flat(4096)
+    lat.run(2)
+    st.run(2, TILE, TILE, 0.95, 0.05, 1, 0)
+    _same(lat, st, "L=4096")
+
+
+def test_execution_knobs_do_not_change_result(eng):
+    ref = None
+    for run in (1, 2, 4, 8):
+        for wpc in (1, 3, 8):
+            lat = eng.Lattice(1024, 0.9, 0.1, seed=12, run=run, warps_per_cta=wpc)
+            lat.run(5)
+            w = lat.slopes()
+            if ref is None:
+                ref = (w, lat.roughness())
+            else:
+                assert np.array_equal(w, ref[0]), (run, wpc)
+                assert lat.roughness() == ref[1]
+
+
+def test_resume_is_bit_exact(eng):
+    a = eng.Lattice(512, 0.7, 0.2, seed=4, sample=3)
+    a.run(7)
+    words, r = a.slopes(), a.roughness()
+    b = eng.Lattice(512, 0.7, 0.2, seed=4, sample=3)
+    b.set_slopes(words, h00=r["h00"], t=7)
+    a.run(5)
+    b.run(5)
+    assert np.array_equal(a.slopes(), b.slopes())
+    assert a.roughness() == b.roughness()
+
+
+def test_rerun_is_deterministic(eng):
+    outs = []
+    for _ in range(2):
+        lat = eng.Lattice(2048, 1.0, 0.0, seed=5)
+        lat.run(10)
+        outs.append((lat.slopes(), lat.roughness()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
