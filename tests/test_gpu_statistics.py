@@ -1,0 +1,75 @@
+"""Statistics of the decomposed dynamics on the GPU (arXiv:1204.5072, Sec. 3:
+the decomposition must not change the physics).
+
+* Growth exponent: W^2 ~ t^(2 beta) in the growth regime; for the 2+1-d KPZ
+  class beta ~ 0.24 (p = 1, q = 0, L = 512, t in [50, 2000]).
+* Random-sequential reference: the ensemble mean of W^2(t) from the GPU
+  agrees with the oracle's random-sequential-update runs (no decomposition)
+  within the early-time offset of single-hit double tiling (about 3-5 % for
+  t <= 64) and within errors later.
+* lambda = 0 (p = q): Edwards-Wilkinson class, much slower (logarithmic) growth.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from synth import inputs as I
+from tests.gpu_util import engine
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eng():
+    return engine()
+
+
+def _ensemble(eng, L, p, q, ts, n, seed=1):
+    W = np.zeros((n, len(ts)))
+    for k in range(n):
+        lat = eng.Lattice(L, p, q, seed=seed, sample=k)
+        t0 = 0
+        for j, t in enumerate(ts):
+            if t > t0:
+                lat.run(t - t0)
+            W[k, j] = lat.roughness()["w2"]
+            t0 = t
+        lat.close()
+    return W
+
+
+def test_growth_exponent_beta(eng):
+    ts = [t for t in I.sample_times(2000) if t >= 50]
+    W = _ensemble(eng, 512, 1.0, 0.0, ts, 16)
+    m = W.mean(axis=0)
+    slope = np.polyfit(np.log(ts), np.log(m), 1)[0]
+    beta = slope / 2
+    assert 0.20 < beta < 0.27, beta
+
+
+def test_matches_random_sequential_reference(eng):
+    L, ts, n = 128, [1, 2, 4, 8, 16, 32, 64, 128], 24
+    gpu = _ensemble(eng, L, 1.0, 0.0, ts, 64, seed=11)
+    rsu = np.zeros((n, len(ts)))
+    for k in range(n):
+        st = O.State.flat(L)
+        for j, t in enumerate(ts):
+            st.rsu(t - st.t, 1.0, 0.0, seed=12, sample=k)
+            rsu[k, j] = st.w2()
+    mg, mr = gpu.mean(0), rsu.mean(0)
+    err = np.sqrt(gpu.var(0, ddof=1) / gpu.shape[0] + rsu.var(0, ddof=1) / n)
+    rel = mg / mr - 1
+    assert np.all(np.abs(rel) < 0.07), rel
+    assert np.all(np.abs(mg - mr) < 0.07 * mr + 4 * err)
+    # growth exponents over t in [8, 128] agree
+    sel = slice(3, None)
+    bg = np.polyfit(np.log(ts[sel]), np.log(mg[sel]), 1)[0] / 2
+    br = np.polyfit(np.log(ts[sel]), np.log(mr[sel]), 1)[0] / 2
+    assert abs(bg - br) < 0.03, (bg, br)
+
+
+def test_edwards_wilkinson_grows_slower(eng):
+    ts = [8, 512]
+    kpz = _ensemble(eng, 256, 1.0, 0.0, ts, 4).mean(0)
+    ew = _ensemble(eng, 256, 0.5, 0.5, ts, 4).mean(0)
+    assert ew[1] / ew[0] < 0.6 * kpz[1] / kpz[0]
