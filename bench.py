@@ -247,8 +247,9 @@ def main():
     n_sweeps = sum(n for _, _, n in sweep_events)
     per_sweep_s = sweep_ms / 1e3 / n_sweeps
 
-    # Roofline of the sweep kernel: 2 slope bits read + 2 written per site.
-    alg_bytes = 0.5 * L * L
+    # Roofline of the sweep kernel: the state is one bit per site (the height
+    # bit (h >> 1) & 1); a sweep reads and writes it once: 0.25 B per attempt.
+    alg_bytes = 0.25 * L * L
     peak, peak_kind = peaks()
     achieved = alg_bytes / per_sweep_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -303,7 +304,7 @@ def main():
                                        f"{len(times)} log-spaced times, 1 realisation per GPU",
                            "L": L, "p": w.p, "q": w.q, "mcs": mcs, "samples": len(times),
                            "tile": "128x128, 4x4 cells", "seed": w.seed,
-                           "l2": "lattice (L^2/4 bytes) larger than L2", "parallelism": f"replicas{world}"},
+                           "l2": "lattice (L^2/8 bytes = 512 MiB at L=2^16) larger than L2", "parallelism": f"replicas{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk.summary(), "gpu_launches": launches,
                 "w2_final": rough[-1]["w2"]}

@@ -29,7 +29,9 @@
  * Packed exchange format (kpz_slopes / kpz_set_slopes): row j (y) occupies
  * L/16 consecutive 32-bit words; site i (x) sits in word j*(L/16) + i/16 at bit
  * 2*(i%16) (sigma_x, 1 = +1) and bit 2*(i%16)+1 (sigma_y). The engine's own
- * HBM layout is different (bit-sliced per cell row) and is not part of the ABI.
+ * HBM layout is different and is not part of the ABI: one bit per site,
+ * (h >> 1) & 1, which with the fixed site parity h = i + j + h(0,0) (mod 2)
+ * determines every slope; bit-sliced per 4 x 4 cell row.
  */
 #ifndef KPZ_H
 #define KPZ_H
@@ -121,8 +123,8 @@ kpz_status kpz_slopes(kpz_ctx* ctx, uint32_t* host_out);
  * to t_mcs. Validity is the caller's responsibility. Synchronises.          */
 kpz_status kpz_set_slopes(kpz_ctx* ctx, const uint32_t* host_in, int64_t h00, uint64_t t_mcs);
 
-/* Device pointer of the lattice and its size in bytes (for callers that keep
- * the lattice resident and time kernels on the context stream). */
+/* Device pointer of the lattice and its size in bytes, L*L/8 (for callers that
+ * keep the lattice resident and time kernels on the context stream). */
 kpz_status kpz_device_lattice(kpz_ctx* ctx, void** dev_ptr, size_t* bytes);
 
 /* Number of kernels this library has launched in the process so far (all

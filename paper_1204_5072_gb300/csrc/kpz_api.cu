@@ -8,7 +8,7 @@
 #include <new>
 #include <string>
 
-#include "../../include/kpz.h"
+#include "kpz.h"
 #include "kpz_internal.h"
 
 using namespace kpz;
@@ -28,10 +28,11 @@ struct kpz_ctx {
   bool own_buf = false;
   void* buf = nullptr;
   size_t buf_bytes = 0;
-  uint32_t* lat = nullptr;             // L*L/16 words
+  uint32_t* lat = nullptr;             // L*L/32 words (one bit per site)
   uint64_t* t_dev = nullptr;           // sweep counter
   unsigned long long* h00 = nullptr;   // absolute height of site (0,0)
   unsigned long long* acc = nullptr;   // S1, S2 lo, S2 hi
+  uint32_t* hcar = nullptr;            // import: height of (0, j0) modulo 4
   int32_t* col0 = nullptr;             // h(0,j)
   void* io = nullptr;                  // staging band for host transfers
   size_t io_bytes = 0;
@@ -55,9 +56,9 @@ struct Layout {
 
 Layout layout(uint32_t L) {
   Layout y{};
-  const size_t lat_bytes = (size_t)L * L / 4;   // 2 bits per site
+  const size_t lat_bytes = (size_t)L * L / 8;   // 1 bit per site
   y.lat = 0;
-  y.small = align_up(lat_bytes);                 // t, h00, acc[3]
+  y.small = align_up(lat_bytes);                 // t, h00, acc[3], hcar
   y.col0 = y.small + kAlign;
   y.io = y.col0 + align_up((size_t)L * 4);
   const size_t io_bytes = std::min(kIoMax, (size_t)L * L * 8);
@@ -180,13 +181,14 @@ kpz_status kpz_init(kpz_ctx** out, uint32_t L, double p, double q, uint64_t seed
   ctx->g.L = L;
   ctx->g.NR = L / 4;
   ctx->g.NB = L / 128;
+  ctx->g.par = 0;
   ctx->Tp = threshold(p);
   ctx->Tq = threshold(q);
   ctx->nlev = levels(ctx->Tp, ctx->Tq);
   ctx->seed = seed;
   ctx->sample = sample;
   ctx->run = o.run ? o.run : auto_run(L);
-  ctx->wpc = o.warps_per_cta ? o.warps_per_cta : 8u;
+  ctx->wpc = o.warps_per_cta ? o.warps_per_cta : 4u;
   ctx->stream = (cudaStream_t)o.stream;
   if (o.dev_buf) {
     ctx->buf = o.dev_buf;
@@ -206,6 +208,7 @@ kpz_status kpz_init(kpz_ctx** out, uint32_t L, double p, double q, uint64_t seed
   ctx->t_dev = (uint64_t*)(base + y.small);
   ctx->h00 = (unsigned long long*)(base + y.small + 8);
   ctx->acc = (unsigned long long*)(base + y.small + 16);
+  ctx->hcar = (uint32_t*)(base + y.small + 40);
   ctx->col0 = (int32_t*)(base + y.col0);
   ctx->io = base + y.io;
   ctx->io_bytes = y.total - y.io;
@@ -225,6 +228,7 @@ kpz_status kpz_reset(kpz_ctx* ctx) {
   KPZ_CUDA(cudaMemsetAsync(ctx->t_dev, 0, 2 * sizeof(uint64_t), ctx->stream));
   KPZ_CUDA(launch_init_flat(ctx->lat, ctx->g, ctx->stream));
   ctx->t_host = 0;
+  ctx->g.par = 0;
   return KPZ_OK;
 }
 
@@ -312,11 +316,16 @@ kpz_status kpz_set_slopes(kpz_ctx* ctx, const uint32_t* host_in, int64_t h00, ui
   const uint32_t L = ctx->g.L;
   const size_t row_bytes = (size_t)L / 16 * 4;
   const uint32_t band = (uint32_t)std::min<size_t>(L, ctx->io_bytes / row_bytes) & ~3u;
+  ctx->g.par = (uint32_t)(h00 & 1);
+  const uint32_t h00_mod4 = (uint32_t)(h00 & 3);
+  KPZ_CUDA(cudaMemcpyAsync(ctx->hcar, &h00_mod4, sizeof(uint32_t), cudaMemcpyHostToDevice,
+                           ctx->stream));
   for (uint32_t j0 = 0; j0 < L; j0 += band) {
     const uint32_t nr = std::min(band, L - j0);
     KPZ_CUDA(cudaMemcpyAsync(ctx->io, (const char*)host_in + (size_t)j0 * row_bytes, nr * row_bytes,
                              cudaMemcpyHostToDevice, ctx->stream));
-    KPZ_CUDA(launch_import_packed(ctx->lat, ctx->g, j0, nr, (const uint32_t*)ctx->io, ctx->stream));
+    KPZ_CUDA(launch_import_packed(ctx->lat, ctx->g, j0, nr, (const uint32_t*)ctx->io, ctx->hcar,
+                                  ctx->col0, ctx->stream));
     KPZ_CUDA(cudaStreamSynchronize(ctx->stream));
   }
   unsigned long long small[2] = {(unsigned long long)t_mcs, (unsigned long long)h00};
@@ -329,7 +338,7 @@ kpz_status kpz_set_slopes(kpz_ctx* ctx, const uint32_t* host_in, int64_t h00, ui
 kpz_status kpz_device_lattice(kpz_ctx* ctx, void** dev_ptr, size_t* bytes) {
   if (!ctx || !dev_ptr || !bytes) return KPZ_EINVAL;
   *dev_ptr = ctx->lat;
-  *bytes = (size_t)ctx->g.L * ctx->g.L / 4;
+  *bytes = (size_t)ctx->g.L * ctx->g.L / 8;
   return KPZ_OK;
 }
 

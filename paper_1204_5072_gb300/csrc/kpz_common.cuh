@@ -1,15 +1,26 @@
 // kpz_common.cuh -- device-side building blocks shared by the engine's kernels.
 //
+// State encoding. Every move changes a height by +-2 (eq. rule), so a site's
+// height keeps the parity h(i,j) = i + j + par (mod 2) with par = h(0,0) mod 2
+// of the start surface. Its height modulo 4 is therefore fixed by one bit,
+//   b(i,j) = (h(i,j) >> 1) & 1,      h mod 4 = 2 b + (i + j + par) mod 2,
+// and the octahedron slopes follow from neighbouring bits:
+//   neighbour n of site s is higher than s  <=>  b(n) ^ b(s) = (i_s + j_s + par) & 1,
+//   sigma_x(i,j) = +1 <=> b(i+1,j) ^ b(i,j) = (i+j+par) & 1, likewise sigma_y.
+// A flip (h -> h +- 2) toggles b of that one site. One bit per site is the
+// information content of the surface; the 2-bit slope format of the paper
+// (Sec. 2.1) is kept as the exchange format of the C ABI.
+//
 // HBM layout of a lattice of lateral size L (bit-sliced cell rows):
 //   storage cell = 4 x 4 sites; cell row R = sites with y in [4R, 4R+4), R < L/4;
 //   block column K = 32 consecutive storage cells along x (128 sites), K < L/128;
-//   plane p = (y%4 * 4 + x%4) * 2 + sigma, sigma 0 = slope in x, 1 = slope in y.
-//   word(K, p, R) = lat[(K*32 + p) * (L/4) + R]; bit c of it is the sigma-slope
-//   (1 = +1) of site (128K + 4c + x%4, 4R + y%4).
-// Each word holds one slope bit of 32 cells, so one logic instruction updates
-// 32 cells ("multi-spin coding" of the bit-coded cellular automaton the paper
-// relies on, Sec. 5). Lanes of a warp read consecutive R: loads and stores of
-// a warp cover 128 contiguous bytes. The layout holds 2 bits per site.
+//   plane p = (y%4) * 4 + x%4.
+//   word(K, p, R) = lat[(K*16 + p) * (L/4) + R]; bit c of it is b of site
+//   (128K + 4c + x%4, 4R + y%4).
+// One word holds the bit of 32 cells, so one logic instruction updates 32
+// cells ("multi-spin coding" of the bit-coded cellular automaton, Sec. 5).
+// Lanes of a warp read consecutive R: a warp's load or store of one plane
+// covers 128 contiguous bytes.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -40,18 +51,18 @@ enum : uint32_t { kTagOrigin = 0u, kTagSet = 1u, kTagPos = 2u, kTagAcc = 3u };
 
 constexpr uint32_t kTile = 128;      // tile edge in sites (device layer)
 constexpr uint32_t kRounds = 16;     // single-hit rounds per sweep = sites per cell
+constexpr uint32_t kPlanes = 16;     // bit planes per cell row
 
 struct Geometry {
   uint32_t L;        // lateral size (power of two, >= 128)
   uint32_t NR;       // L/4 cell rows
   uint32_t NB;       // L/128 block columns
+  uint32_t par;      // parity of h(0,0) of the start surface
   __host__ __device__ size_t word(uint32_t K, uint32_t p, uint32_t R) const {
-    return ((size_t)K * 32u + p) * NR + R;
+    return ((size_t)K * kPlanes + p) * NR + R;
   }
 };
 
-__host__ __device__ constexpr uint32_t plane(uint32_t y4, uint32_t x4, uint32_t sigma) {
-  return (y4 * 4u + x4) * 2u + sigma;
-}
+__host__ __device__ constexpr uint32_t plane(uint32_t y4, uint32_t x4) { return y4 * 4u + x4; }
 
 }  // namespace kpz

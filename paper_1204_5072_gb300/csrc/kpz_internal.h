@@ -32,12 +32,14 @@ cudaError_t launch_advance(uint64_t* t_dev, uint32_t n, cudaStream_t st);
 
 // Observables and conversions (kpz_observe.cu).
 cudaError_t launch_init_flat(uint32_t* lat, Geometry g, cudaStream_t st);
-// Packed exchange format, rows [j0, j0 + nrows) <-> packed[(j - j0) * L/16 + i/16];
-// for the import j0 and nrows are multiples of 4.
+// Packed exchange format, rows [j0, j0 + nrows) <-> packed[(j - j0) * L/16 + i/16].
+// The import walks the bands in order: *hcar carries the absolute height of
+// site (0, j0) modulo 4 from band to band; hcol is scratch for nrows int32.
 cudaError_t launch_export_packed(const uint32_t* lat, Geometry g, uint32_t j0, uint32_t nrows,
                                  uint32_t* packed, cudaStream_t st);
 cudaError_t launch_import_packed(uint32_t* lat, Geometry g, uint32_t j0, uint32_t nrows,
-                                 const uint32_t* packed, cudaStream_t st);
+                                 const uint32_t* packed, uint32_t* hcar, int32_t* hcol,
+                                 cudaStream_t st);
 
 // Exact height sums, eq. Wdef: col0[L] (int32) and acc[3] (S1, S2 lo, S2 hi)
 // are scratch that the caller provides.

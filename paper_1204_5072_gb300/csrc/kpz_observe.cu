@@ -2,6 +2,8 @@
 //
 // Sec. 2.1 of arXiv:1204.5072: flat start with periodic boundaries, heights
 // reconstructed from the slopes, squared interface width eq. (Wdef).
+// The lattice holds one bit per site, b = (h >> 1) & 1 (kpz_common.cuh); the
+// slopes follow from neighbouring bits and the site parity (i + j + par) & 1.
 // Heights are built in the gauge h(0,0) = 0: first down column 0,
 //   h(0,j) = sum_{k<j} sigma_y(0,k),
 // then along each row, h(i,j) = h(0,j) + sum_{l<i} sigma_x(l,j); on a valid
@@ -11,18 +13,34 @@
 namespace kpz {
 namespace {
 
-// Flat start: h = (i+j) & 1, so every slope is +1 where i+j is even. In the
-// bit-sliced layout the parity of a site is (x%4 + y%4) % 2, the same for all
-// 32 cells of a word.
-__global__ void init_flat_kernel(uint4* lat4, Geometry g, size_t n4) {
+__device__ __forceinline__ uint32_t parity_mask(uint32_t v) { return (v & 1u) ? ~0u : 0u; }
+
+// Bit b of site (i, j) (i < L, j < L).
+__device__ __forceinline__ uint32_t site_bit(const uint32_t* lat, const Geometry& g, uint32_t i,
+                                             uint32_t j) {
+  return (lat[g.word(i >> 7, plane(j & 3u, i & 3u), j >> 2)] >> ((i >> 2) & 31u)) & 1u;
+}
+
+// Flat start h = (i+j) & 1: h >> 1 = 0 everywhere.
+__global__ void init_flat_kernel(uint4* lat4, size_t n4) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const size_t w = i * 4;                 // 4 consecutive words share K and p
-    const uint32_t p = (uint32_t)((w / g.NR) & 31u);
-    const uint32_t y4 = p >> 3, x4 = (p >> 1) & 3u;
-    const uint32_t v = ((x4 + y4) & 1u) ? 0u : ~0u;
-    lat4[i] = make_uint4(v, v, v, v);
-  }
+       i += (size_t)gridDim.x * blockDim.x)
+    lat4[i] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// Bits of 4 consecutive cells (starting at cell c0) of a plane, spread to
+// positions 4*jc (jc = cell offset): the row-major order of sites 4jc + x4.
+__device__ __forceinline__ uint32_t spread4(uint32_t n) {
+  return (n & 1u) | ((n & 2u) << 3) | ((n & 4u) << 6) | ((n & 8u) << 9);
+}
+
+// Interleave: bit k of a -> bit 2k, for a < 2^16.
+__device__ __forceinline__ uint32_t part1by1(uint32_t a) {
+  a = (a | (a << 8)) & 0x00FF00FFu;
+  a = (a | (a << 4)) & 0x0F0F0F0Fu;
+  a = (a | (a << 2)) & 0x33333333u;
+  a = (a | (a << 1)) & 0x55555555u;
+  return a;
 }
 
 // One packed word (16 sites of row j) per thread.
@@ -33,58 +51,89 @@ __global__ void export_kernel(const uint32_t* __restrict__ lat, Geometry g, uint
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
        idx += (size_t)gridDim.x * blockDim.x) {
     const uint32_t j = j0 + (uint32_t)(idx / wpr), wi = (uint32_t)(idx % wpr);
-    const uint32_t K = wi >> 3, c0 = (wi & 7u) * 4u, R = j >> 2, y4 = j & 3u;
-    uint32_t out = 0;
+    const uint32_t j1 = (j + 1u) & (g.L - 1u);
+    const uint32_t K = wi >> 3, c0 = (wi & 7u) * 4u;
+    uint32_t r0 = 0, r1 = 0;  // bits of sites 16wi + k, k = 0..15, rows j and j+1
 #pragma unroll
-    for (uint32_t x4 = 0; x4 < 4; ++x4)
-#pragma unroll
-      for (uint32_t sg = 0; sg < 2; ++sg) {
-        const uint32_t P = lat[g.word(K, plane(y4, x4, sg), R)] >> c0;
-#pragma unroll
-        for (uint32_t jc = 0; jc < 4; ++jc)
-          out |= ((P >> jc) & 1u) << (2u * (4u * jc + x4) + sg);
-      }
-    packed[idx] = out;
-  }
-}
-
-// One lattice word (K, p, R) per thread for cell rows [R0, R0 + nR), gathered
-// from 8 packed words of the band that starts at row 4*R0.
-__global__ void import_kernel(uint32_t* __restrict__ lat, Geometry g, uint32_t R0, uint32_t nR,
-                              const uint32_t* __restrict__ packed) {
-  const size_t n = (size_t)nR * 32u * g.NB;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t R = R0 + (uint32_t)(idx % nR);
-    const size_t rest = idx / nR;
-    const uint32_t p = (uint32_t)(rest & 31u), K = (uint32_t)(rest >> 5);
-    const size_t w = g.word(K, p, R);
-    const uint32_t y4 = p >> 3, x4 = (p >> 1) & 3u, sg = p & 1u;
-    const uint32_t j = 4u * (R - R0) + y4;
-    const uint32_t* row = packed + (size_t)j * (g.L / 16) + 8u * K;
-    uint32_t v = 0;
-#pragma unroll
-    for (uint32_t q = 0; q < 8; ++q) {
-      const uint32_t pw = row[q];
-#pragma unroll
-      for (uint32_t jc = 0; jc < 4; ++jc)
-        v |= ((pw >> (2u * (4u * jc + x4) + sg)) & 1u) << (4u * q + jc);
+    for (uint32_t x4 = 0; x4 < 4; ++x4) {
+      r0 |= spread4((lat[g.word(K, plane(j & 3u, x4), j >> 2)] >> c0) & 0xFu) << x4;
+      r1 |= spread4((lat[g.word(K, plane(j1 & 3u, x4), j1 >> 2)] >> c0) & 0xFu) << x4;
     }
-    lat[w] = v;
+    r0 |= site_bit(lat, g, (16u * wi + 16u) & (g.L - 1u), j) << 16;
+    // parity of site 16wi + k is (k + j + par) & 1; higher neighbour <=> bits
+    // differ by that parity, so sigma = +1 <=> b(next) ^ b ^ parity == 0
+    const uint32_t odd = ((j + g.par) & 1u) ? 0x5555u : 0xAAAAu;
+    const uint32_t sx = ~((r0 >> 1) ^ r0 ^ odd) & 0xFFFFu;
+    const uint32_t sy = ~(r1 ^ r0 ^ odd) & 0xFFFFu;
+    packed[idx] = part1by1(sx) | (part1by1(sy) << 1);
   }
 }
 
-// h(0,j) for all rows j: one block, chunked sequential sums + block scan.
+// Absolute heights modulo 4 down column 0 for rows [j0, j0 + nrows) of a
+// packed band; hcar holds h(0, j0) mod 4 on entry and h(0, j0 + nrows) mod 4
+// on exit. One block.
+__global__ void import_col_kernel(const uint32_t* __restrict__ packed, Geometry g, uint32_t nrows,
+                                  uint32_t* __restrict__ hcar, int32_t* __restrict__ hcol) {
+  __shared__ int32_t part[1024];
+  const uint32_t nt = blockDim.x, t = threadIdx.x, wpr = g.L / 16;
+  const uint32_t chunk = (nrows + nt - 1) / nt;
+  const uint32_t r0 = min(nrows, t * chunk), r1 = min(nrows, r0 + chunk);
+  int32_t sum = 0;
+  for (uint32_t r = r0; r < r1; ++r) sum += ((packed[(size_t)r * wpr] >> 1) & 1u) ? 1 : -1;
+  part[t] = sum;
+  __syncthreads();
+  for (uint32_t off = 1; off < nt; off <<= 1) {
+    const int32_t v = (t >= off) ? part[t - off] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  const int32_t base = (int32_t)*hcar;
+  int32_t h = base + ((t == 0) ? 0 : part[t - 1]);
+  for (uint32_t r = r0; r < r1; ++r) {
+    hcol[r] = h & 3;
+    h += ((packed[(size_t)r * wpr] >> 1) & 1u) ? 1 : -1;
+  }
+  __syncthreads();
+  if (t == nt - 1) *hcar = (uint32_t)((base + part[nt - 1]) & 3);
+}
+
+// One row of a packed band per thread: walk along the row and store the bits.
+__global__ void import_rows_kernel(uint32_t* __restrict__ lat, Geometry g, uint32_t j0,
+                                   uint32_t nrows, const uint32_t* __restrict__ packed,
+                                   const int32_t* __restrict__ hcol) {
+  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  const uint32_t j = j0 + r, wpr = g.L / 16;
+  const uint32_t* row = packed + (size_t)r * wpr;
+  int32_t h = hcol[r];
+  for (uint32_t K = 0; K < g.NB; ++K) {
+    uint32_t W[4] = {0u, 0u, 0u, 0u};
+    for (uint32_t q = 0; q < 8; ++q) {
+      const uint32_t pw = row[8u * K + q];
+#pragma unroll
+      for (uint32_t k = 0; k < 16; ++k) {  // site 128K + 16q + k = cell 4q + k/4, x4 = k%4
+        W[k & 3u] |= (uint32_t)((h >> 1) & 1) << (4u * q + (k >> 2));
+        h += ((pw >> (2u * k)) & 1u) ? 1 : -1;
+      }
+    }
+#pragma unroll
+    for (uint32_t x4 = 0; x4 < 4; ++x4) lat[g.word(K, plane(j & 3u, x4), j >> 2)] = W[x4];
+  }
+}
+
+// h(0,j) for all rows j, gauge h(0,0) = 0: one block, chunked sums + block scan.
 __global__ void col0_kernel(const uint32_t* __restrict__ lat, Geometry g, int32_t* __restrict__ col0) {
   __shared__ int32_t part[1024];
   const uint32_t nt = blockDim.x, t = threadIdx.x;
   const uint32_t chunk = (g.L + nt - 1) / nt;
-  const uint32_t j0 = t * chunk, j1 = min(g.L, j0 + chunk);
+  const uint32_t j0 = min(g.L, t * chunk), j1 = min(g.L, j0 + chunk);
+  auto step = [&](uint32_t j) -> int32_t {  // sigma_y(0, j)
+    const uint32_t b = site_bit(lat, g, 0, j), bn = site_bit(lat, g, 0, (j + 1u) & (g.L - 1u));
+    return ((b ^ bn) == ((j + g.par) & 1u)) ? 1 : -1;
+  };
   int32_t sum = 0;
-  for (uint32_t j = j0; j < j1; ++j) {
-    const uint32_t bit = lat[g.word(0, plane(j & 3u, 0, 1), j >> 2)] & 1u;  // sigma_y(0,j)
-    sum += 2 * (int32_t)bit - 1;
-  }
+  for (uint32_t j = j0; j < j1; ++j) sum += step(j);
   part[t] = sum;
   __syncthreads();
   for (uint32_t off = 1; off < nt; off <<= 1) {   // inclusive Hillis-Steele scan
@@ -96,8 +145,19 @@ __global__ void col0_kernel(const uint32_t* __restrict__ lat, Geometry g, int32_
   int32_t h = (t == 0) ? 0 : part[t - 1];
   for (uint32_t j = j0; j < j1; ++j) {
     col0[j] = h;
-    const uint32_t bit = lat[g.word(0, plane(j & 3u, 0, 1), j >> 2)] & 1u;
-    h += 2 * (int32_t)bit - 1;
+    h += step(j);
+  }
+}
+
+// sigma_x planes of one 128-site block of row j: bit c of S[x4] is 1 when
+// sigma_x(128K + 4c + x4, j) = +1. P = bit planes of the block, nxt = bit of
+// site 128K + 128.
+__device__ __forceinline__ void sigma_x_planes(const uint32_t (&P)[4], uint32_t nxt, uint32_t j,
+                                               uint32_t par, uint32_t (&S)[4]) {
+#pragma unroll
+  for (uint32_t x4 = 0; x4 < 4; ++x4) {
+    const uint32_t right = (x4 < 3) ? P[x4 < 3 ? x4 + 1 : 0] : ((P[0] >> 1) | (nxt << 31));
+    S[x4] = ~(right ^ P[x4] ^ parity_mask(x4 + j + par));
   }
 }
 
@@ -115,10 +175,16 @@ __global__ void roughness_kernel(const uint32_t* __restrict__ lat, Geometry g,
   if (R < g.NR) {
     const uint32_t j = 4u * R + y4;
     long long H = col0[j];
-    for (uint32_t K = 0; K < g.NB; ++K) {
-      uint32_t P[4];
+    uint32_t P[4];
 #pragma unroll
-      for (uint32_t x4 = 0; x4 < 4; ++x4) P[x4] = __ldcg(lat + g.word(K, plane(y4, x4, 0), R));
+    for (uint32_t x4 = 0; x4 < 4; ++x4) P[x4] = __ldcg(lat + g.word(0, plane(y4, x4), R));
+    for (uint32_t K = 0; K < g.NB; ++K) {
+      uint32_t Pn[4];
+      const uint32_t Kn = (K + 1u) & (g.NB - 1u);
+#pragma unroll
+      for (uint32_t x4 = 0; x4 < 4; ++x4) Pn[x4] = __ldcg(lat + g.word(Kn, plane(y4, x4), R));
+      uint32_t S[4];
+      sigma_x_planes(P, Pn[0] & 1u, j, g.par, S);
       int32_t h = 0, a1 = 0, a2 = 0;
 #pragma unroll 8
       for (uint32_t c = 0; c < 32; ++c)
@@ -126,11 +192,13 @@ __global__ void roughness_kernel(const uint32_t* __restrict__ lat, Geometry g,
         for (uint32_t x4 = 0; x4 < 4; ++x4) {
           a1 += h;
           a2 += h * h;
-          h += 2 * (int32_t)((P[x4] >> c) & 1u) - 1;
+          h += 2 * (int32_t)((S[x4] >> c) & 1u) - 1;
         }
       s1 += 128 * H + a1;
       s2 += (unsigned long long)(128 * H * H + 2 * H * (long long)a1 + (long long)a2);
       H += h;
+#pragma unroll
+      for (uint32_t x4 = 0; x4 < 4; ++x4) P[x4] = Pn[x4];
     }
   }
 #pragma unroll
@@ -156,12 +224,15 @@ __global__ void heights_kernel(const uint32_t* __restrict__ lat, Geometry g,
   for (uint32_t K = 0; K < g.NB; ++K) {
     uint32_t P[4];
 #pragma unroll
-    for (uint32_t x4 = 0; x4 < 4; ++x4) P[x4] = lat[g.word(K, plane(y4, x4, 0), R)];
+    for (uint32_t x4 = 0; x4 < 4; ++x4) P[x4] = lat[g.word(K, plane(y4, x4), R)];
+    const uint32_t nxt = site_bit(lat, g, (128u * K + 128u) & (g.L - 1u), j);
+    uint32_t S[4];
+    sigma_x_planes(P, nxt, j, g.par, S);
     for (uint32_t c = 0; c < 32; ++c)
 #pragma unroll
       for (uint32_t x4 = 0; x4 < 4; ++x4) {
         o[128u * K + 4u * c + x4] = h;
-        h += 2 * (int64_t)((P[x4] >> c) & 1u) - 1;
+        h += 2 * (int64_t)((S[x4] >> c) & 1u) - 1;
       }
   }
 }
@@ -175,8 +246,8 @@ unsigned grid_for(size_t n, unsigned block) {
 }  // namespace
 
 cudaError_t launch_init_flat(uint32_t* lat, Geometry g, cudaStream_t st) {
-  const size_t n4 = (size_t)g.L * g.L / 64;
-  init_flat_kernel<<<grid_for(n4, 256), 256, 0, st>>>(reinterpret_cast<uint4*>(lat), g, n4);
+  const size_t n4 = (size_t)g.L * g.L / 128;   // L^2 bits = L^2/128 uint4
+  init_flat_kernel<<<grid_for(n4, 256), 256, 0, st>>>(reinterpret_cast<uint4*>(lat), n4);
   count_launch();
   return cudaGetLastError();
 }
@@ -189,9 +260,11 @@ cudaError_t launch_export_packed(const uint32_t* lat, Geometry g, uint32_t j0, u
 }
 
 cudaError_t launch_import_packed(uint32_t* lat, Geometry g, uint32_t j0, uint32_t nrows,
-                                 const uint32_t* packed, cudaStream_t st) {
-  const uint32_t R0 = j0 / 4u, nR = nrows / 4u;
-  import_kernel<<<grid_for((size_t)nR * 32u * g.NB, 256), 256, 0, st>>>(lat, g, R0, nR, packed);
+                                 const uint32_t* packed, uint32_t* hcar, int32_t* hcol,
+                                 cudaStream_t st) {
+  import_col_kernel<<<1, 1024, 0, st>>>(packed, g, nrows, hcar, hcol);
+  count_launch();
+  import_rows_kernel<<<(nrows + 127) / 128, 128, 0, st>>>(lat, g, j0, nrows, packed, hcol);
   count_launch();
   return cudaGetLastError();
 }
