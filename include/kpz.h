@@ -50,7 +50,8 @@ typedef enum {
     KPZ_ECUDA = 3,    /* a CUDA call failed; the context is now poisoned      */
     KPZ_ETIMEOUT = 4, /* a bounded device-side wait gave up                   */
     KPZ_ESTATE = 5,   /* context poisoned by an earlier error                 */
-    KPZ_ENODEV = 6    /* no usable CUDA device                                */
+    KPZ_ENODEV = 6,   /* no usable CUDA device                                */
+    KPZ_ERANGE = 7    /* size beyond the fixed scratch of kpz_roughness_static */
 } kpz_status;
 
 typedef struct kpz_ctx kpz_ctx;
@@ -126,6 +127,33 @@ kpz_status kpz_set_slopes(kpz_ctx* ctx, const uint32_t* host_in, int64_t h00, ui
 /* Device pointer of the lattice and its size in bytes, L*L/8 (for callers that
  * keep the lattice resident and time kernels on the context stream). */
 kpz_status kpz_device_lattice(kpz_ctx* ctx, void** dev_ptr, size_t* bytes);
+
+/* Exact W^2 of a lattice the caller already holds on the device, without
+ * allocating anything. The paper has no counterpart to this call; it exists
+ * for callers that cannot call cudaMalloc when they need the width: work
+ * being captured into a CUDA graph, processes whose device memory is fully
+ * reserved by another framework's caching allocator, or loops that must not
+ * allocate after start-up. It computes what kpz_roughness computes.
+ *   lattice_dev: the lattice in the engine's layout, as returned by
+ *                kpz_device_lattice (L*L/8 bytes, read only);
+ *   L:           its lateral size, a power of two with 128 <= L <= 131072;
+ *   parity:      the parity of the absolute height of site (0,0) of the
+ *                surface the lattice started from (0 for the flat start, h00 & 1
+ *                after kpz_set_slopes);
+ *   stream:      cudaStream_t to queue on (NULL = default stream); the call
+ *                synchronises it;
+ *   out:         host struct; t_mcs and h00 are set to 0 (this call has no
+ *                context that knows them).
+ * Scratch: one static device array of 512 KiB + 256 B per GPU that loads the
+ * library, held until the process exits. L above 131072 returns KPZ_ERANGE;
+ * a null pointer or an L that is not a power of two >= 128 returns
+ * KPZ_EINVAL. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. All calls share the array, which keeps the last
+ * call's contents; the call clears what must start at zero. Calls that
+ * overlap on the GPU (other streams, other host threads) race on the array. */
+kpz_status kpz_roughness_static(const void* lattice_dev, uint32_t L, uint32_t parity,
+                                void* stream, kpz_rough* out);
 
 /* Number of kernels this library has launched in the process so far (all
  * contexts); lets a caller count the GPU work inside a timed region. */

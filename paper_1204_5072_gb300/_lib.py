@@ -12,7 +12,7 @@ import numpy as np
 
 from . import build as _build
 
-KPZ_OK, KPZ_EINVAL, KPZ_ENOMEM, KPZ_ECUDA, KPZ_ETIMEOUT, KPZ_ESTATE, KPZ_ENODEV = range(7)
+KPZ_OK, KPZ_EINVAL, KPZ_ENOMEM, KPZ_ECUDA, KPZ_ETIMEOUT, KPZ_ESTATE, KPZ_ENODEV, KPZ_ERANGE = range(8)
 
 
 class KpzError(RuntimeError):
@@ -58,6 +58,8 @@ def load(path: str | None = None):
     L.kpz_slopes.argtypes = [vp, vp]
     L.kpz_set_slopes.argtypes = [vp, vp, c.c_int64, c.c_uint64]
     L.kpz_device_lattice.argtypes = [vp, c.POINTER(vp), c.POINTER(c.c_size_t)]
+    L.kpz_roughness_static.argtypes = [vp, c.c_uint32, c.c_uint32, vp, c.POINTER(kpz_rough)]
+    L.kpz_roughness_static.restype = c.c_int
     L.kpz_launch_count.argtypes = []
     L.kpz_launch_count.restype = c.c_uint64
     L.kpz_free.argtypes = [vp]

@@ -150,6 +150,7 @@ const char* kpz_strerror(kpz_status st) {
     case KPZ_ETIMEOUT: return "device wait timed out";
     case KPZ_ESTATE: return "context poisoned by an earlier error";
     case KPZ_ENODEV: return "no CUDA device";
+    case KPZ_ERANGE: return "lattice larger than the 131072 maximum of the static scratch";
   }
   return "unknown status";
 }
