@@ -49,12 +49,37 @@ def parse():
 
 
 def peaks():
+    """(HBM GB/s, SM max MHz, source) from the driver-written measurements."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
     except Exception:
-        return 6800.0, "fallback"
+        return 6800.0, 2070.0, "fallback"
+
+
+# ALU-pipe operations the algorithm needs per attempt at p = 1, q = 0 (bit-sliced
+# rule on 32 cells per word, 2 Philox bits per attempt, window staging):
+# 20/64 (Philox xors) + 22/32 (masks, tests, flips, neighbour shifts) + 64/512.
+K_ALG_ALU = 20 / 64 + 22 / 32 + 64 / 512
+ALU_LANES_PER_SM = 64   # integer logic pipe: 16 lanes per SM sub-partition per clock
+
+
+def measured_traffic(L):
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was
+    taken on this size and on the current kernel source; else None."""
+    import hashlib
+    try:
+        src = b"".join(open(os.path.join(ROOT, "paper_1204_5072_gb300", "csrc", f), "rb").read()
+                       for f in ("kpz_sweep.cu", "kpz_common.cuh"))
+        sha = hashlib.sha256(src).hexdigest()[:16]
+        txt = open(os.path.join(ROOT, "profiles", "sweep_kernel_L65536.md")).read()
+        fields = dict(ln.split(": ", 1) for ln in txt.splitlines() if ": " in ln and ln[:1].isalpha())
+        if L == 65536 and fields.get("source_sha256") == sha:
+            return float(fields["traffic_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
 
 
 # --------------------------------------------------------------------------- #
@@ -247,15 +272,23 @@ def main():
     n_sweeps = sum(n for _, _, n in sweep_events)
     per_sweep_s = sweep_ms / 1e3 / n_sweeps
 
-    # Roofline of the sweep kernel: the state is one bit per site (the height
-    # bit (h >> 1) & 1); a sweep reads and writes it once: 0.25 B per attempt.
+    # Roofline of the sweep kernel. The state is one bit per site, read and
+    # written once per sweep (0.25 B/attempt); the integer-logic pipe binds
+    # first: K_ALG_ALU ops per attempt against 152 SMs x 64 lanes x clock.
+    hbm_peak, sm_mhz, peak_kind = peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
     alg_bytes = 0.25 * L * L
-    peak, peak_kind = peaks()
-    achieved = alg_bytes / per_sweep_s / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "sweep_kernel",
-                "alg_bytes_per_launch": alg_bytes, "launch_ms": per_sweep_s * 1e3,
-                "peak_source": f"{peak_kind} hbm_gbs"}
+    alu_peak = sms * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e12          # Top/s
+    alu_achieved = K_ALG_ALU * L * L / per_sweep_s / 1e12
+    hbm_achieved = alg_bytes / per_sweep_s / 1e9
+    roofline = {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "Top/s",
+                "frac": alu_achieved / alu_peak, "traffic": measured_traffic(L),
+                "kernel": "sweep_kernel", "alg_ops_per_attempt": K_ALG_ALU,
+                "launch_ms": per_sweep_s * 1e3,
+                "peak_source": f"{sms} SMs x {ALU_LANES_PER_SM} ALU lanes x {sm_mhz:.0f} MHz ({peak_kind} clock)",
+                "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": hbm_achieved / hbm_peak, "alg_bytes_per_launch": alg_bytes,
+                        "peak_source": f"{peak_kind} hbm_gbs"}}
 
     # End to end through the C ABI with host buffers: upload the start state
     # from pinned memory, run the job with W^2 sampling, read the final lattice.
