@@ -128,6 +128,71 @@ kpz_status kpz_set_slopes(kpz_ctx* ctx, const uint32_t* host_in, int64_t h00, ui
  * keep the lattice resident and time kernels on the context stream). */
 kpz_status kpz_device_lattice(kpz_ctx* ctx, void** dev_ptr, size_t* bytes);
 
+/* ------------------------------------------------------------------------ */
+/* Batched ensemble: many independent realisations in one persistent launch. */
+/* ------------------------------------------------------------------------ */
+/* Each realisation is its own lattice run exactly as kpz_init + kpz_run would
+ * run it (flat start, Sec. 2.1; decomposition of Sec. 3; same Philox streams),
+ * so its W^2 sums equal those of a kpz_ctx with the same arguments. The paper
+ * runs one lattice per GPU (Sec. 4); this call serves ensembles of unequal
+ * lattices, whose small members alone would leave most of the GPU idle.    */
+typedef struct kpz_batch kpz_batch;
+
+typedef struct {
+    uint32_t L;          /* lateral size: power of two, 128 <= L <= 131072        */
+    double p, q;         /* attachment / detachment probabilities (eq. rule)      */
+    uint64_t seed;       /* Philox key                                            */
+    uint32_t sample;     /* realisation index (Philox counter word)               */
+    uint32_t n_mcs;      /* sweeps to run                                         */
+} kpz_spec;
+
+typedef struct {
+    void* stream;          /* cudaStream_t (NULL = default stream)                 */
+    uint32_t n_samples;    /* log-spaced W^2 times up to the longest run (0 = 64);
+                              every realisation is also sampled at its own end    */
+    int autotune;          /* != 0: time a short probe of the ensemble for every
+                              (tiles per run, warps per block) and keep the fastest;
+                              the choice never changes the results                */
+    uint32_t run;          /* tiles per run when not tuning (power of two, 0 = 4)  */
+    uint32_t warps_per_cta;/* 1..8 (0 = 8)                                         */
+    uint32_t ctas_per_sm;  /* resident blocks per SM (0 = as many as fit)          */
+    uint32_t timeout_ms;   /* bound of every device-side wait (0 = 10000)          */
+    int32_t test_block;    /* tests only: index (in run-length order, longest
+                              first) of a realisation whose waits can never
+                              succeed, to exercise the timeout; -1 = none        */
+} kpz_batch_opts;
+
+typedef struct {
+    uint32_t run, warps_per_cta, ctas_per_sm, grid;  /* chosen execution knobs       */
+    int graph;                                       /* 1: launched from a CUDA graph */
+    uint64_t items;                                  /* work items in the queue       */
+    uint32_t n_probe;                                /* autotune probes timed         */
+    double probe_ms[8];                              /* their times                   */
+} kpz_batch_info;
+
+/* Validate the specs (KPZ_EINVAL: bad L, p or q), allocate all lattices and
+ * tables (KPZ_ENOMEM), optionally autotune, and capture the run in a graph.
+ * opts may be NULL (defaults; test_block then -1).                          */
+kpz_status kpz_batch_create(kpz_batch** out, const kpz_spec* specs, uint32_t n,
+                            const kpz_batch_opts* opts);
+/* Run every realisation from the flat start to its n_mcs with W^2 sampled at
+ * the batch's sample times: one persistent cooperative launch. Synchronises.
+ * KPZ_ETIMEOUT if a device-side wait ran out of time (the launch then stops
+ * early and the batch may be run again).                                    */
+kpz_status kpz_batch_run(kpz_batch* b);
+/* Sample times (ascending, starting at 0). *n: capacity in, count out; times
+ * may be NULL to query the count.                                           */
+kpz_status kpz_batch_times(const kpz_batch* b, uint64_t* times, uint32_t* n);
+/* Exact sums after kpz_batch_run, caller order, row-major [spec][time]
+ * (n x n_times each); entries for times beyond a spec's n_mcs are 0. h00
+ * (may be NULL): absolute height of site (0,0) of each lattice at its end.  */
+kpz_status kpz_batch_sums(const kpz_batch* b, int64_t* S1, uint64_t* S2_lo, uint64_t* S2_hi,
+                          int64_t* h00);
+/* W^2 = (N S2 - S1^2) / N^2 (eq. Wdef), n x n_times, NaN beyond a spec's end. */
+kpz_status kpz_batch_w2(const kpz_batch* b, double* w2);
+kpz_status kpz_batch_get_info(const kpz_batch* b, kpz_batch_info* out);
+void kpz_batch_free(kpz_batch* b);
+
 /* Exact W^2 of a lattice the caller already holds on the device, without
  * allocating anything. The paper has no counterpart to this call; it exists
  * for callers that cannot call cudaMalloc when they need the width: work

@@ -200,3 +200,117 @@ class Lattice:
 
     def __exit__(self, *a):
         self.close()
+
+
+# --------------------------------------------------------------------------- #
+# Batched ensemble (kpz_batch_* in include/kpz.h)
+class kpz_spec(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_uint32), ("p", ctypes.c_double), ("q", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("sample", ctypes.c_uint32), ("n_mcs", ctypes.c_uint32)]
+
+
+class kpz_batch_opts(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_void_p), ("n_samples", ctypes.c_uint32), ("autotune", ctypes.c_int),
+                ("run", ctypes.c_uint32), ("warps_per_cta", ctypes.c_uint32),
+                ("ctas_per_sm", ctypes.c_uint32), ("timeout_ms", ctypes.c_uint32),
+                ("test_block", ctypes.c_int32)]
+
+
+class kpz_batch_info(ctypes.Structure):
+    _fields_ = [("run", ctypes.c_uint32), ("warps_per_cta", ctypes.c_uint32),
+                ("ctas_per_sm", ctypes.c_uint32), ("grid", ctypes.c_uint32), ("graph", ctypes.c_int),
+                ("items", ctypes.c_uint64), ("n_probe", ctypes.c_uint32),
+                ("probe_ms", ctypes.c_double * 8)]
+
+
+def _bind_batch(L):
+    c = ctypes
+    vp = c.c_void_p
+    L.kpz_batch_create.argtypes = [c.POINTER(vp), c.POINTER(kpz_spec), c.c_uint32, c.POINTER(kpz_batch_opts)]
+    L.kpz_batch_run.argtypes = [vp]
+    L.kpz_batch_times.argtypes = [vp, vp, c.POINTER(c.c_uint32)]
+    L.kpz_batch_sums.argtypes = [vp, vp, vp, vp, vp]
+    L.kpz_batch_w2.argtypes = [vp, vp]
+    L.kpz_batch_get_info.argtypes = [vp, c.POINTER(kpz_batch_info)]
+    L.kpz_batch_free.argtypes = [vp]
+    L.kpz_batch_free.restype = None
+    for fn in ("kpz_batch_create", "kpz_batch_run", "kpz_batch_times", "kpz_batch_sums",
+               "kpz_batch_w2", "kpz_batch_get_info"):
+        getattr(L, fn).restype = c.c_int
+
+
+class Batch:
+    """Independent realisations (L, p, q, seed, sample, n_mcs) run in one
+    persistent launch; results match single Lattice runs bit for bit."""
+
+    def __init__(self, specs, n_samples=0, autotune=False, run=0, warps_per_cta=0, ctas_per_sm=0,
+                 timeout_ms=0, test_block=-1, stream=None):
+        lib = load()
+        if not hasattr(lib, "_batch_bound"):
+            _bind_batch(lib)
+            lib._batch_bound = True
+        self.specs = [tuple(s) for s in specs]
+        arr = (kpz_spec * len(self.specs))()
+        for k, (L, p, q, seed, sample, n) in enumerate(self.specs):
+            arr[k] = kpz_spec(int(L), float(p), float(q), int(seed), int(sample), int(n))
+        o = kpz_batch_opts()
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream().cuda_stream
+            except ImportError:
+                pass
+        o.stream = stream or None
+        o.n_samples, o.autotune, o.run = n_samples, int(bool(autotune)), run
+        o.warps_per_cta, o.ctas_per_sm, o.timeout_ms, o.test_block = warps_per_cta, ctas_per_sm, timeout_ms, test_block
+        self._b = ctypes.c_void_p()
+        check(lib.kpz_batch_create(ctypes.byref(self._b), arr, len(self.specs), ctypes.byref(o)))
+
+    def run(self) -> "Batch":
+        check(load().kpz_batch_run(self._b))
+        return self
+
+    def times(self) -> np.ndarray:
+        n = ctypes.c_uint32(0)
+        check(load().kpz_batch_times(self._b, None, ctypes.byref(n)))
+        out = np.zeros(n.value, np.uint64)
+        check(load().kpz_batch_times(self._b, _ptr(out), ctypes.byref(n)))
+        return out
+
+    def sums(self):
+        """(S1, S2 as Python ints) arrays of shape (n_specs, n_times), and h00."""
+        n, m = len(self.specs), len(self.times())
+        s1 = np.zeros((n, m), np.int64)
+        lo = np.zeros((n, m), np.uint64)
+        hi = np.zeros((n, m), np.uint64)
+        h = np.zeros(n, np.int64)
+        check(load().kpz_batch_sums(self._b, _ptr(s1), _ptr(lo), _ptr(hi), _ptr(h)))
+        s2 = np.empty((n, m), object)
+        for i in range(n):
+            for k in range(m):
+                s2[i, k] = (int(hi[i, k]) << 64) | int(lo[i, k])
+        return s1, s2, h
+
+    def w2(self) -> np.ndarray:
+        out = np.zeros((len(self.specs), len(self.times())), np.float64)
+        check(load().kpz_batch_w2(self._b, _ptr(out)))
+        return out
+
+    def info(self) -> dict:
+        i = kpz_batch_info()
+        check(load().kpz_batch_get_info(self._b, ctypes.byref(i)))
+        return {"run": i.run, "warps_per_cta": i.warps_per_cta, "ctas_per_sm": i.ctas_per_sm,
+                "grid": i.grid, "graph": bool(i.graph), "items": i.items,
+                "probe_ms": list(i.probe_ms)[:i.n_probe]}
+
+    def close(self):
+        if getattr(self, "_b", None):
+            load().kpz_batch_free(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -66,18 +66,6 @@ Layout layout(uint32_t L) {
   return y;
 }
 
-uint32_t threshold(double p) {
-  if (!(p > 0.0)) return 0u;
-  if (p >= 1.0) return 65536u;
-  const double t = std::floor(p * 65536.0 + 0.5);
-  return t >= 65536.0 ? 65536u : (uint32_t)t;
-}
-
-uint32_t levels(uint32_t Tp, uint32_t Tq) {
-  const uint32_t low = (Tp & 0xFFFFu) | (Tq & 0xFFFFu);
-  if (!low) return 0u;
-  return 16u - (uint32_t)__builtin_ctz(low);
-}
 
 kpz_status fail(kpz_ctx* c, kpz_status st, const std::string& msg) {
   if (c) {
@@ -183,9 +171,9 @@ kpz_status kpz_init(kpz_ctx** out, uint32_t L, double p, double q, uint64_t seed
   ctx->g.NR = L / 4;
   ctx->g.NB = L / 128;
   ctx->g.par = 0;
-  ctx->Tp = threshold(p);
-  ctx->Tq = threshold(q);
-  ctx->nlev = levels(ctx->Tp, ctx->Tq);
+  ctx->Tp = acceptance_threshold(p);
+  ctx->Tq = acceptance_threshold(q);
+  ctx->nlev = acceptance_levels(ctx->Tp, ctx->Tq);
   ctx->seed = seed;
   ctx->sample = sample;
   ctx->run = o.run ? o.run : auto_run(L);

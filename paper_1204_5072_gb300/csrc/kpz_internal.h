@@ -11,6 +11,22 @@ namespace kpz {
 // Process-wide count of kernel launches issued by this library.
 void count_launch(uint64_t n = 1);
 
+// Acceptance threshold out of 2^16 for a per-attempt probability (eq. rule):
+// min(65536, floor(p * 65536 + 0.5)); an attempt accepts when its uniform
+// 16-bit number U < T, so p = 1 always and p = 0 never accepts.
+inline uint32_t acceptance_threshold(double p) {
+  if (!(p > 0.0)) return 0u;
+  if (p >= 1.0) return 65536u;
+  const double t = __builtin_floor(p * 65536.0 + 0.5);
+  return t >= 65536.0 ? 65536u : (uint32_t)t;
+}
+
+// Bit levels of U that can still change a comparison with Tp or Tq.
+inline uint32_t acceptance_levels(uint32_t Tp, uint32_t Tq) {
+  const uint32_t low = (Tp & 0xFFFFu) | (Tq & 0xFFFFu);
+  return low ? 16u - (uint32_t)__builtin_ctz(low) : 0u;
+}
+
 // One sweep (one MCS) of the decomposed dynamics, Sec. 3 and 3.1.
 struct SweepParams {
   uint32_t* lat;            // lattice words (layout in kpz_common.cuh)
