@@ -193,6 +193,34 @@ kpz_status kpz_batch_w2(const kpz_batch* b, double* w2);
 kpz_status kpz_batch_get_info(const kpz_batch* b, kpz_batch_info* out);
 void kpz_batch_free(kpz_batch* b);
 
+/* ------------------------------------------------------------------------ */
+/* Learned surrogate of W^2(t; L, p, q) (not part of the paper).             */
+/* ------------------------------------------------------------------------ */
+/* A 4-128-128-128-1 multilayer perceptron with GELU hidden units, bfloat16
+ * weights and float32 arithmetic, trained by the library's own forward,
+ * backward and Adam kernels. Parameters: one float32 vector of 33793 values,
+ * W1 (128 x 4, row-major), b1 (128), W2 (128 x 128), b2, W3 (128 x 128), b3,
+ * w4 (128), b4 (1). Inputs: n rows of 4 float32 features; targets: n float32.
+ * The loss is the mean squared error. Gradients are reduced in a fixed order:
+ * a call with the same inputs gives the same result.                       */
+typedef struct kpz_mlp kpz_mlp;
+/* Upload initial parameters (caller-chosen initialisation); stream may be NULL. */
+kpz_status kpz_mlp_create(kpz_mlp** out, const float* params, void* stream);
+/* Current float32 master parameters (33793 values).                         */
+kpz_status kpz_mlp_params(kpz_mlp* m, float* params);
+/* y[i] = network(x[i]) with the bfloat16 weights.                           */
+kpz_status kpz_mlp_predict(kpz_mlp* m, const float* x, uint32_t n, float* y);
+/* Mean squared error over the n samples and its gradient (33793 values).   */
+kpz_status kpz_mlp_loss_grad(kpz_mlp* m, const float* x, const float* t, uint32_t n, float* loss,
+                             float* grad);
+/* `steps` Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr);
+ * step s uses samples order[s*batch .. s*batch+batch-1] of (x, t), order
+ * holding steps*batch indices < n. last_loss: the loss of the last minibatch
+ * before its update. The Adam moments persist across calls.               */
+kpz_status kpz_mlp_train(kpz_mlp* m, const float* x, const float* t, uint32_t n, const uint32_t* order,
+                         uint32_t steps, uint32_t batch, float lr, float* last_loss);
+void kpz_mlp_free(kpz_mlp* m);
+
 /* Exact W^2 of a lattice the caller already holds on the device, without
  * allocating anything. The paper has no counterpart to this call; it exists
  * for callers that cannot call cudaMalloc when they need the width: work

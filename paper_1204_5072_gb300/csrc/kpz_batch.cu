@@ -458,7 +458,7 @@ kpz_status prepare(kpz_batch* b, const std::vector<uint64_t>* cap_T) {
     saved = b->spec;
     saved_times = b->times;
     for (uint32_t c = 0; c < n; ++c) b->spec[c].n_mcs = (uint32_t)(*cap_T)[c];
-    b->times = sample_grid(b->spec, 4);
+    b->times = sample_grid(b->spec, 2);   // start and end only: the probe times sweeping
   }
   HostPlan hp = build_plan(b, real);
   const size_t nseg_max = 2 * (cap_T ? saved_times.size() : b->times.size()) + 4;
@@ -561,10 +561,11 @@ kpz_status kpz_batch_create(kpz_batch** out, const kpz_spec* specs, uint32_t n, 
   if (st) return fail_free(b, st);
 
   if (o.autotune) {
-    // Time a short probe of the same ensemble (every run capped at a few
-    // sweeps) for each setting of the execution knobs; keep the fastest.
+    // Time a short probe of the same ensemble (every run capped at 24 sweeps,
+    // W^2 only at its start and end) for each setting of the execution knobs;
+    // keep the fastest (first in this order on ties).
     std::vector<uint64_t> cap(n);
-    for (uint32_t c = 0; c < n; ++c) cap[c] = std::min<uint64_t>(b->spec[c].n_mcs, 4);
+    for (uint32_t c = 0; c < n; ++c) cap[c] = std::min<uint64_t>(b->spec[c].n_mcs, 24);
     const uint32_t runs[] = {1, 2, 4, 8}, wpcs[] = {4, 8};
     float best = 1e30f;
     uint32_t best_run = 4, best_wpc = 8;
