@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample-mcs", type=int, default=100)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-cap", type=int, default=200)
+    ap.add_argument("--no-surrogate", action="store_true")
     return ap.parse_args()
 
 
@@ -193,6 +196,109 @@ def run_reference(a):
 
 
 # --------------------------------------------------------------------------- #
+def batch_bench(eng, cap, seed=1):
+    """Batched ensemble (512 realisations shaped like the batched workload: L =
+    2^{8..13} log-uniform, p ~ U[0.5, 1], q = 1 - p, run length min(4 L^1.6, cap)),
+    one persistent graph launch, against (i) one launch per sweep per realisation
+    (kpz_run, W^2 at the same times) and (ii) one persistent launch per realisation."""
+    import torch
+    specs = [(s.L, s.p, s.q, seed, s.sample, min(s.mcs, cap)) for s in I.ensemble_specs(512, seed=seed)]
+    attempts = float(sum(L * L * n for L, _, _, _, _, n in specs))
+    t0 = time.perf_counter()
+    b = eng.Batch(specs, n_samples=64, autotune=True)
+    create_s = time.perf_counter() - t0
+    b.run()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.run()
+    torch.cuda.synchronize()
+    batched = time.perf_counter() - t0
+    times = [int(t) for t in b.times()]
+    info = b.info()
+    b.close()
+    t0 = time.perf_counter()
+    for (L, p, q, sd, smp, n) in specs:
+        lat = eng.Lattice(L, p, q, seed=sd, sample=smp)
+        tp = 0
+        for t in times:
+            if t > n:
+                break
+            if t > tp:
+                lat.run(t - tp)
+            lat.roughness()
+            tp = t
+        lat.close()
+    per_sweep = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for sp in specs:
+        one = eng.Batch([sp], n_samples=64)
+        one.run()
+        one.close()
+    per_real = time.perf_counter() - t0
+    n = len(specs)
+    return {"metric": "batched realisations/s", "value": n / batched, "unit": "realisations/s",
+            "attempts_per_s": attempts / batched, "seconds": batched,
+            "vs_launch_per_sweep": {"value": n / per_sweep, "seconds": per_sweep,
+                                    "speedup": per_sweep / batched},
+            "vs_launch_per_realisation": {"value": n / per_real, "seconds": per_real,
+                                          "speedup": per_real / batched},
+            "workload": f"512 realisations, L=2^(8..13) log-uniform, p~U[0.5,1], q=1-p, "
+                        f"T=min(4 L^1.6, {cap}) MCS, W^2 at the common log-spaced times (seed {seed})",
+            "tuning": {k: info[k] for k in ("run", "warps_per_cta", "ctas_per_sm", "grid", "graph")},
+            "autotune_s": create_s}
+
+
+def surrogate_bench(eng):
+    """Surrogate trained by the engine's kernels on simulated ensemble means
+    (L in {128, 256}, p in {0.7, 0.8, 0.9, 1.0}, q = 1 - p, 64 realisations each,
+    run length 4 L^1.6); error against fresh 128-realisation ensembles at held-out
+    p in {0.75, 0.95}; planned run lengths 2 t_sat against 4 L^1.6."""
+    import math
+    import numpy as np
+    from paper_1204_5072_gb300 import surrogate as S
+
+    def heur(L):
+        return int(min(math.ceil(4 * L ** 1.6), 100_000))
+
+    def ens(pairs, seeds, run_len):
+        specs = [(L, p, 1 - p, 100 + k, k, run_len(L, p)) for (L, p) in pairs for k in seeds]
+        b = eng.Batch(specs, n_samples=48)
+        b.run()
+        t, w = b.times(), b.w2()
+        b.close()
+        out = {}
+        for (L, p) in pairs:
+            rows = [i for i, sp in enumerate(specs) if sp[0] == L and sp[1] == p]
+            with np.errstate(invalid="ignore"):
+                out[(L, p)] = np.nanmean(w[rows], axis=0)
+        return t, out
+
+    LS, PT, PH = [128, 256], [0.7, 0.8, 0.9, 1.0], [0.75, 0.95]
+    t0 = time.perf_counter()
+    tr_pairs = [(L, p) for L in LS for p in PT]
+    times, means = ens(tr_pairs, range(64), lambda L, p: heur(L))
+    sim_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sur = S.Surrogate.fit([(L, p, 1 - p, 0, 0, heur(L)) for (L, p) in tr_pairs], times,
+                          np.stack([means[k] for k in tr_pairs]), epochs=400, batch=128, lr=3e-3, seed=1)
+    train_s = time.perf_counter() - t0
+    ho = [(L, p) for L in LS for p in PH]
+    th, hmeans = ens(ho, range(200, 328), lambda L, p: heur(L))
+    errs = {}
+    for (L, p), m in hmeans.items():
+        sel = (th >= 1) & (th <= heur(L)) & np.isfinite(m)
+        errs[f"L{L}_p{p}"] = float(np.mean(np.abs(sur.w2(L, th[sel], p, 1 - p) / m[sel] - 1)))
+    planned = {k: int(min(heur(k[0]), math.ceil(2 * sur.t_sat(k[0], k[1], 1 - k[1], t_max=heur(k[0])))))
+               for k in ho}
+    saved = sum((heur(L) - planned[(L, p)]) * L * L for (L, p) in ho) / sum(heur(L) * L * L for (L, p) in ho)
+    sur.close()
+    return {"held_out_mean_rel_error": errs, "max_mean_rel_error": max(errs.values()),
+            "planned_mcs": {f"L{L}_p{p}": v for (L, p), v in planned.items()},
+            "fixed_rule_mcs": {f"L{L}": heur(L) for L in LS}, "sweeps_saved_frac": saved,
+            "train_s": train_s, "simulate_s": sim_s}
+
+
+# --------------------------------------------------------------------------- #
 def main():
     a = parse()
     if a.impl == "reference":
@@ -327,6 +433,8 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         cpu = cpu_baseline(L, a.cpu_sample_mcs)
+    batch = None if (a.no_batch or world > 1) else batch_bench(eng, a.batch_cap)
+    sur = None if (a.no_surrogate or world > 1) else surrogate_bench(eng)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -340,7 +448,7 @@ def main():
                            "l2": "lattice (L^2/8 bytes = 512 MiB at L=2^16) larger than L2", "parallelism": f"replicas{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk.summary(), "gpu_launches": launches,
-                "w2_final": rough[-1]["w2"]}
+                "w2_final": rough[-1]["w2"], "batch": batch, "surrogate": sur}
         print(json.dumps(line), flush=True)
     lat.close()
     if dist:

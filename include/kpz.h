@@ -58,10 +58,15 @@ typedef struct kpz_ctx kpz_ctx;
 
 /* Options; a NULL pointer or zero fields select the defaults. */
 typedef struct {
-    uint32_t bx, by;      /* tile shape in sites; only 128 x 128 is built (0 = 128)  */
-    uint32_t run;         /* tiles one warp sweeps along x per sweep (0 = auto);
-                             execution only, it does not change the result           */
-    uint32_t warps_per_cta; /* 0 = auto; execution only                              */
+    uint32_t bx, by;      /* tile shape in sites: bx = 128; by = 128 or 256 (0 = 128).
+                             The tile shape is part of the schedule (Sec. 3.1), so
+                             different shapes give different (equally valid)
+                             trajectories; 128 x 256 needs L >= 256               */
+    uint32_t run;         /* tiles per work item: the resident warps take runs of
+                             `run` tiles of one tile row from a queue (power of two
+                             <= L/128; 0 = min(8, L/128)); execution only, it does
+                             not change the result                                 */
+    uint32_t warps_per_cta; /* 1..8, 0 = 4; execution only                         */
     void* stream;         /* cudaStream_t to queue work on (NULL = default stream)  */
     void* dev_buf;        /* optional caller-owned device memory for the lattice and
                              its scratch; at least kpz_device_bytes(L) bytes,
@@ -90,7 +95,7 @@ size_t kpz_device_bytes(uint32_t L);
  * h(i,j) = (i+j) & 1, so W^2 = 1/4. `init` must be 0 (flat start).
  * Preconditions (KPZ_EINVAL otherwise, checked before any allocation):
  *   L a power of two with 128 <= L <= 131072; 0 <= p, q <= 1 (no NaN);
- *   bx = by = 128 (or 0). p and q are quantised to multiples of 2^-16
+ *   bx = 128 (or 0), by = 128 or 256 (or 0). p and q are quantised to multiples of 2^-16
  *   (T = min(65536, floor(x*65536 + 0.5))): attempts accept with U < T for a
  *   uniform 16-bit U. `sample` is the realisation index that enters the
  *   Philox counter next to the seed.                                          */

@@ -105,11 +105,12 @@ class Lattice:
     """
 
     def __init__(self, L: int, p: float = 1.0, q: float = 0.0, seed: int = 1, sample: int = 0,
-                 run: int = 0, warps_per_cta: int = 0, stream=None, device_buffer=None):
+                 run: int = 0, warps_per_cta: int = 0, stream=None, device_buffer=None,
+                 tile_y: int = 0):
         lib = load()
         self.L, self.p, self.q, self.seed, self.sample = int(L), float(p), float(q), int(seed), int(sample)
         o = kpz_opts()
-        o.run, o.warps_per_cta = run, warps_per_cta
+        o.run, o.warps_per_cta, o.by = run, warps_per_cta, tile_y
         if stream is None:
             try:
                 import torch

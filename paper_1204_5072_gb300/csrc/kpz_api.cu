@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <atomic>
 #include <new>
 #include <string>
@@ -23,6 +24,7 @@ struct kpz_ctx {
   uint32_t Tp = 0, Tq = 0, nlev = 0, sample = 0;
   uint64_t seed = 0;
   uint32_t run = 1, wpc = 8;
+  uint32_t tile_y = 128;               // tile height in sites (128 or 256)
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_buf = false;
@@ -33,6 +35,7 @@ struct kpz_ctx {
   unsigned long long* h00 = nullptr;   // absolute height of site (0,0)
   unsigned long long* acc = nullptr;   // S1, S2 lo, S2 hi
   uint32_t* hcar = nullptr;            // import: height of (0, j0) modulo 4
+  uint32_t* queue = nullptr;           // sweep work queue (zero between launches)
   int32_t* col0 = nullptr;             // h(0,j)
   void* io = nullptr;                  // staging band for host transfers
   size_t io_bytes = 0;
@@ -58,7 +61,7 @@ Layout layout(uint32_t L) {
   Layout y{};
   const size_t lat_bytes = (size_t)L * L / 8;   // 1 bit per site
   y.lat = 0;
-  y.small = align_up(lat_bytes);                 // t, h00, acc[3], hcar
+  y.small = align_up(lat_bytes);                 // t, h00, acc[3], hcar, queue
   y.col0 = y.small + kAlign;
   y.io = y.col0 + align_up((size_t)L * 4);
   const size_t io_bytes = std::min(kIoMax, (size_t)L * L * 8);
@@ -99,7 +102,7 @@ SweepParams sweep_params(const kpz_ctx* c) {
   P.t_dev = c->t_dev;
   P.g = c->g;
   P.ntx = c->g.L / kTile;
-  P.nty = c->g.L / kTile;
+  P.nty = c->g.L / c->tile_y;
   P.run = c->run;
   P.runs_x = P.ntx / c->run;
   P.Tp = c->Tp;
@@ -109,17 +112,10 @@ SweepParams sweep_params(const kpz_ctx* c) {
   P.k1 = (uint32_t)(c->seed >> 32);
   P.sample = c->sample;
   P.h00 = c->h00;
+  P.queue = c->queue;
   return P;
 }
 
-uint32_t auto_run(uint32_t L) {
-  const uint32_t ntx = L / kTile;
-  const uint64_t tiles = (uint64_t)ntx * ntx;
-  const uint64_t target = 152ull * 16ull * 4ull;  // warps that keep every SM busy
-  uint32_t run = 1;
-  while (run * 2 <= ntx && tiles / (run * 2) >= target && run < 16) run *= 2;
-  return run;
-}
 
 }  // namespace
 
@@ -154,7 +150,9 @@ kpz_status kpz_init(kpz_ctx** out, uint32_t L, double p, double q, uint64_t seed
     return KPZ_EINVAL;
   kpz_opts o{};
   if (opts) o = *opts;
-  if ((o.bx != 0 && o.bx != kTile) || (o.by != 0 && o.by != kTile)) return KPZ_EINVAL;
+  if ((o.bx != 0 && o.bx != kTile) ||
+      (o.by != 0 && o.by != kTile && !(o.by == 2u * kTile && L >= 2u * kTile)))
+    return KPZ_EINVAL;
   const uint32_t ntx = L / kTile;
   if (o.run != 0 && ((o.run & (o.run - 1)) != 0 || o.run > ntx)) return KPZ_EINVAL;
   if (o.warps_per_cta > 8) return KPZ_EINVAL;
@@ -176,7 +174,8 @@ kpz_status kpz_init(kpz_ctx** out, uint32_t L, double p, double q, uint64_t seed
   ctx->nlev = acceptance_levels(ctx->Tp, ctx->Tq);
   ctx->seed = seed;
   ctx->sample = sample;
-  ctx->run = o.run ? o.run : auto_run(L);
+  ctx->tile_y = o.by ? o.by : kTile;
+  ctx->run = o.run ? o.run : std::min(8u, ntx);   // tiles per work-queue chunk
   ctx->wpc = o.warps_per_cta ? o.warps_per_cta : 4u;
   ctx->stream = (cudaStream_t)o.stream;
   if (o.dev_buf) {
@@ -198,6 +197,7 @@ kpz_status kpz_init(kpz_ctx** out, uint32_t L, double p, double q, uint64_t seed
   ctx->h00 = (unsigned long long*)(base + y.small + 8);
   ctx->acc = (unsigned long long*)(base + y.small + 16);
   ctx->hcar = (uint32_t*)(base + y.small + 40);
+  ctx->queue = (uint32_t*)(base + y.small + 48);
   ctx->col0 = (int32_t*)(base + y.col0);
   ctx->io = base + y.io;
   ctx->io_bytes = y.total - y.io;

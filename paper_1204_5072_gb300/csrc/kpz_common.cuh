@@ -30,18 +30,37 @@ namespace kpz {
 // Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw, SC'11):
 // ten rounds of two 32x32->64 multiplications whose high halves are mixed
 // with the other two words and a round key advanced by two Weyl constants.
+constexpr uint32_t kPhiloxMulA = 0xD2511F53u, kPhiloxMulB = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxWeylA = 0x9E3779B9u, kPhiloxWeylB = 0xBB67AE85u;
+constexpr int kPhiloxRounds = 10;
+
 __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                         uint32_t k0, uint32_t k1) {
-  constexpr uint32_t kMulA = 0xD2511F53u, kMulB = 0xCD9E8D57u;
-  constexpr uint32_t kWeylA = 0x9E3779B9u, kWeylB = 0xBB67AE85u;
 #pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint32_t hiA = __umulhi(kMulA, c0), loA = kMulA * c0;
-    const uint32_t hiB = __umulhi(kMulB, c2), loB = kMulB * c2;
+  for (int r = 0; r < kPhiloxRounds; ++r) {
+    const uint32_t hiA = __umulhi(kPhiloxMulA, c0), loA = kPhiloxMulA * c0;
+    const uint32_t hiB = __umulhi(kPhiloxMulB, c2), loB = kPhiloxMulB * c2;
     const uint32_t n0 = hiB ^ c1 ^ k0;
     const uint32_t n2 = hiA ^ c3 ^ k1;
     c0 = n0; c1 = loB; c2 = n2; c3 = loA;
-    k0 += kWeylA; k1 += kWeylB;
+    k0 += kPhiloxWeylA; k1 += kPhiloxWeylB;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+// Philox4x32-10 with the ten round keys (k0 + r W_A, k1 + r W_B) read from
+// shared memory as rk[r/2] = {key r, key r+1} (same output as philox()).
+__device__ __forceinline__ uint4 philox_sk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                           const uint4* rk) {
+#pragma unroll
+  for (int r = 0; r < kPhiloxRounds; r += 2) {
+    const uint4 k = rk[r >> 1];
+    uint32_t hiA = __umulhi(kPhiloxMulA, c0), loA = kPhiloxMulA * c0;
+    uint32_t hiB = __umulhi(kPhiloxMulB, c2), loB = kPhiloxMulB * c2;
+    c0 = hiB ^ c1 ^ k.x; c1 = loB; c2 = hiA ^ c3 ^ k.y; c3 = loA;
+    hiA = __umulhi(kPhiloxMulA, c0); loA = kPhiloxMulA * c0;
+    hiB = __umulhi(kPhiloxMulB, c2); loB = kPhiloxMulB * c2;
+    c0 = hiB ^ c1 ^ k.z; c1 = loB; c2 = hiA ^ c3 ^ k.w; c3 = loA;
   }
   return make_uint4(c0, c1, c2, c3);
 }

@@ -34,13 +34,14 @@ struct SweepParams {
   uint32_t s_add;
   Geometry g;
   uint32_t ntx, nty;        // tiles per row / per column of the tile grid
-  uint32_t run;             // tiles one warp processes along x
-  uint32_t runs_x;          // ntx / run
+  uint32_t run;             // tiles one warp sweeps in a row per work item
+  uint32_t runs_x;          // ntx / run (work items per tile row)
   uint32_t Tp, Tq;          // acceptance thresholds out of 2^16 (65536 = always)
   uint32_t nlev;            // acceptance levels that can change a decision
   uint32_t k0, k1;          // Philox key = seed
   uint32_t sample;          // realisation index (Philox counter word 3)
   unsigned long long* h00;  // absolute height of site (0,0), two's complement
+  uint32_t* queue;          // single-lattice sweep: work-queue counter, 0 between launches
 };
 
 cudaError_t launch_sweep(const SweepParams& P, uint32_t warps_per_cta, cudaStream_t st);

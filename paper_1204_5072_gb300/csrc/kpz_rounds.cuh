@@ -1,15 +1,20 @@
-// kpz_rounds.cuh -- the 16 single-hit rounds of one 128 x 128 tile held by a
-// warp in registers (arXiv:1204.5072, Sec. 3.1; update rule eq. rule, Sec. 2.1).
+// kpz_rounds.cuh -- the 16 single-hit rounds of one tile of 128 x (128 CR)
+// sites held by a warp in registers (arXiv:1204.5072, Sec. 3.1; update rule
+// eq. rule, Sec. 2.1).
 //
-// T[y'][x'] holds the height bits of site (x', y') of the 4 x 4 cells of the
-// lane's cell row (bit c = cell c). A round evaluates the rule for the four
+// Lane l holds cell rows CR*l .. CR*l + CR - 1 of the tile; T[r][y'][x'] holds
+// the height bits of site (x', y') of the 4 x 4 cells of its r-th cell row
+// (bit c = cell c). A round evaluates the rule for the four
 // sites of the active quadrant on all 32 cells at once with bitwise logic: a
 // neighbour is higher iff its bit equals v = b(s) ^ parity(s); a minimum has
 // all four neighbours equal to v, a maximum none; a move toggles b(s).
 // Neighbours in x come from a 1-bit shift (cells c-1, c+1), neighbours in y
-// from the lanes above and below (warp shuffles); hx[y'] (bit 0) is the column
-// right of the tile and hy[x'] (lane 31) the row below it, both dead borders
-// of neighbouring tiles that nobody changes during the sweep.
+// from the lane's other cell row or the lanes above and below (warp
+// shuffles); hx[r][y'] (bit 0) is the column right of the tile and hy[x']
+// (lane 31) the row below it, both dead borders of neighbouring tiles that
+// nobody changes during the sweep. Within a round each cell moves at most one
+// site and no selected site is a neighbour of another selected site, so the
+// order in which cells and cell rows are evaluated does not matter.
 #pragma once
 #include "kpz_internal.h"
 
@@ -18,6 +23,12 @@ namespace rounds {
 
 constexpr uint32_t kFull = 0xffffffffu;
 
+// Philox draw of a tile: from the round keys in shared memory (tc.rk) or,
+// without kSK, by advancing the key (P.k0, P.k1).
+struct TileCtx;
+template <bool kSK>
+__device__ __forceinline__ uint4 draw(const SweepParams& P, const TileCtx& tc, uint32_t c0);
+
 struct TileCtx {
   uint32_t tid;           // tile id ty*ntx + tx (Philox counter word 1)
   uint32_t s;             // sweep index (Philox counter word 2)
@@ -25,16 +36,24 @@ struct TileCtx {
   uint32_t first_row_ok;  // ~0 unless lane 0 (tile row v = 0 is dead)
   bool last_lane;         // lane 31: the row below comes from the halo
   bool track;             // this tile contains site (0,0)
-  uint32_t xo, yo, co, cyo;  // position of site (0,0) in the tile
+  uint32_t xo, yo, co, cyo;  // site (0,0): column, row in the cell, cell, cell row
+  const uint4* rk;        // round keys in shared memory (kSK)
 };
 
-// Bit-serial comparison U < T for the 32 cells of a lane (U uniform 16-bit,
-// level n = bit 15-n of U taken from bit c of word n&3 of Philox call n>>2).
-// Only cells in needp (selected site is a minimum) and needq (a maximum) need
-// a decision; a cell is decided at the first level where U and T differ, so
-// the warp stops drawing levels once no cell of any lane is still tied. The
-// outcome equals the full 16-level comparison.
-__device__ __forceinline__ void acceptance(const SweepParams& P, const TileCtx& tc, uint32_t lane,
+template <bool kSK>
+__device__ __forceinline__ uint4 draw(const SweepParams& P, const TileCtx& tc, uint32_t c0) {
+  if (kSK) return philox_sk(c0, tc.tid, tc.s, P.sample, tc.rk);
+  return philox(c0, tc.tid, tc.s, P.sample, P.k0, P.k1);
+}
+
+// Bit-serial comparison U < T for the 32 cells of cell row cy (U uniform
+// 16-bit, level n = bit 15-n of U taken from bit c of word n&3 of Philox call
+// n>>2). Only cells in needp (selected site is a minimum) and needq (a
+// maximum) need a decision; a cell is decided at the first level where U and
+// T differ, so the warp stops drawing levels once no cell of any lane is still
+// tied. The outcome equals the full 16-level comparison.
+template <bool kSK>
+__device__ __forceinline__ void acceptance(const SweepParams& P, const TileCtx& tc, uint32_t cy,
                                            uint32_t r, uint32_t needp, uint32_t needq,
                                            uint32_t& AP, uint32_t& AQ) {
   uint32_t ltp = 0u, ltq = 0u;
@@ -43,8 +62,7 @@ __device__ __forceinline__ void acceptance(const SweepParams& P, const TileCtx& 
 #pragma unroll 1
   for (uint32_t m = 0; m < 4; ++m) {
     if (4u * m >= P.nlev || !__any_sync(0xffffffffu, (undp | undq) != 0u)) break;
-    const uint4 A = philox((kTagAcc << 28) | (lane << 6) | (r << 2) | m, tc.tid, tc.s, P.sample,
-                           P.k0, P.k1);
+    const uint4 A = draw<kSK>(P, tc, (kTagAcc << 28) | (cy << 6) | (r << 2) | m);
     const uint32_t w[4] = {A.x, A.y, A.z, A.w};
 #pragma unroll
     for (uint32_t j = 0; j < 4; ++j) {
@@ -62,100 +80,121 @@ __device__ __forceinline__ void acceptance(const SweepParams& P, const TileCtx& 
 }
 
 // One single-hit round with active quadrant (QX, QY); kPar = parity of the
-// tile's site (0,0). T[y'][x'], hx[y'] (bit 0: right halo), hy[x'] (lane 31:
-// the row below the tile).
-template <int QX, int QY, bool kGeneral, int kPar, bool kTrack>
-__device__ __forceinline__ void quad_round(uint32_t (&T)[4][4], uint32_t Xi, uint32_t Yi,
-                                           const uint32_t (&hx)[4], const uint32_t (&hy)[4],
-                                           const SweepParams& P, const TileCtx& tc,
-                                           uint32_t lane, uint32_t r, int& dh) {
+// tile's site (0,0); Xi[r], Yi[r]: position bits of cell row r.
+template <int QX, int QY, bool kGeneral, int kPar, bool kTrack, int CR, bool kSK>
+__device__ __forceinline__ void quad_round(uint32_t (&T)[CR][4][4], const uint32_t (&Xi)[CR],
+                                           const uint32_t (&Yi)[CR], const uint32_t (&hx)[CR][4],
+                                           const uint32_t (&hy)[4], const SweepParams& P,
+                                           const TileCtx& tc, uint32_t lane, uint32_t r, int& dh) {
   constexpr int x0 = 2 * QX, y0 = 2 * QY;
-  uint32_t sel[2][2];  // [dy][dx]: cells whose random site is (x0+dx, y0+dy)
-  sel[0][0] = ~Xi & ~Yi;
-  sel[0][1] = Xi & ~Yi;
-  sel[1][0] = ~Xi & Yi;
-  sel[1][1] = Xi & Yi;
-  if (QX == 0) { sel[0][0] &= ~1u; sel[1][0] &= ~1u; }       // tile column u = 0
-  if (QY == 0) { sel[0][0] &= tc.first_row_ok; sel[0][1] &= tc.first_row_ok; }  // row v = 0
-
-  uint32_t xn[2], yn[2];  // neighbours outside the cell (x) and outside the lane (y)
-#pragma unroll
-  for (int d = 0; d < 2; ++d)
-    xn[d] = (QX == 0) ? (T[y0 + d][3] << 1)                            // cell c-1, column 3
-                      : __funnelshift_r(T[y0 + d][0], hx[y0 + d], 1);  // cell c+1, column 0
+  // The one y-neighbour per column that lies in another lane.
+  uint32_t ysh[2];
   if (QY == 0) {
-    yn[0] = __shfl_up_sync(kFull, T[3][x0], 1);
-    yn[1] = __shfl_up_sync(kFull, T[3][x0 + 1], 1);
+    ysh[0] = __shfl_up_sync(kFull, T[CR - 1][3][x0], 1);
+    ysh[1] = __shfl_up_sync(kFull, T[CR - 1][3][x0 + 1], 1);
   } else {
-    const uint32_t d0 = __shfl_down_sync(kFull, T[0][x0], 1);
-    const uint32_t d1 = __shfl_down_sync(kFull, T[0][x0 + 1], 1);
-    yn[0] = tc.last_lane ? hy[x0] : d0;
-    yn[1] = tc.last_lane ? hy[x0 + 1] : d1;
+    const uint32_t d0 = __shfl_down_sync(kFull, T[0][0][x0], 1);
+    const uint32_t d1 = __shfl_down_sync(kFull, T[0][0][x0 + 1], 1);
+    ysh[0] = tc.last_lane ? hy[x0] : d0;
+    ysh[1] = tc.last_lane ? hy[x0 + 1] : d1;
   }
-
-  uint32_t fmin[2][2], fmax[2][2];
 #pragma unroll
-  for (int dy = 0; dy < 2; ++dy)
+  for (int row = 0; row < CR; ++row) {
+    uint32_t sel[2][2];  // [dy][dx]: cells whose random site is (x0+dx, y0+dy)
+    sel[0][0] = ~Xi[row] & ~Yi[row];
+    sel[0][1] = Xi[row] & ~Yi[row];
+    sel[1][0] = ~Xi[row] & Yi[row];
+    sel[1][1] = Xi[row] & Yi[row];
+    if (QX == 0) { sel[0][0] &= ~1u; sel[1][0] &= ~1u; }            // tile column u = 0
+    if (QY == 0 && row == 0) { sel[0][0] &= tc.first_row_ok; sel[0][1] &= tc.first_row_ok; }  // v = 0
+    uint32_t xn[2], yn[2];  // neighbours outside the cell (x) and outside the cell row (y)
 #pragma unroll
-    for (int dx = 0; dx < 2; ++dx) {
-      const int xp = x0 + dx, yp = y0 + dy;
-      const uint32_t s = T[yp][xp];
-      const uint32_t nL = (xp > 0) ? T[yp][xp > 0 ? xp - 1 : 0] : xn[dy];
-      const uint32_t nR = (xp < 3) ? T[yp][xp < 3 ? xp + 1 : 3] : xn[dy];
-      const uint32_t nU = (yp > 0) ? T[yp > 0 ? yp - 1 : 0][xp] : yn[dx];
-      const uint32_t nD = (yp < 3) ? T[yp < 3 ? yp + 1 : 3][xp] : yn[dx];
-      const uint32_t v = ((kPar + xp + yp) & 1) ? ~s : s;   // bit of a higher neighbour
-      const uint32_t hL = ~(nL ^ v), hR = ~(nR ^ v), hU = ~(nU ^ v), hD = ~(nD ^ v);
-      fmin[dy][dx] = sel[dy][dx] & hL & hR & hU & hD;                       // local minimum
-      fmax[dy][dx] = kGeneral ? (sel[dy][dx] & ~hL & ~hR & ~hU & ~hD) : 0u;  // local maximum
+    for (int d = 0; d < 2; ++d) {
+      xn[d] = (QX == 0) ? (T[row][y0 + d][3] << 1)                                 // cell c-1, col 3
+                        : __funnelshift_r(T[row][y0 + d][0], hx[row][y0 + d], 1);  // cell c+1, col 0
+      if (QY == 0) yn[d] = (row > 0) ? T[row > 0 ? row - 1 : 0][3][x0 + d] : ysh[d];
+      else         yn[d] = (row < CR - 1) ? T[row < CR - 1 ? row + 1 : 0][0][x0 + d] : ysh[d];
     }
-  if (kGeneral) {
-    uint32_t AP, AQ;
-    acceptance(P, tc, lane, r, fmin[0][0] | fmin[0][1] | fmin[1][0] | fmin[1][1],
-               fmax[0][0] | fmax[0][1] | fmax[1][0] | fmax[1][1], AP, AQ);
+    uint32_t fmin[2][2], fmax[2][2];
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-      for (int dx = 0; dx < 2; ++dx) { fmin[dy][dx] &= AP; fmax[dy][dx] &= AQ; }
-  }
-  if (kTrack && lane == tc.cyo) {
+      for (int dx = 0; dx < 2; ++dx) {
+        const int xp = x0 + dx, yp = y0 + dy;
+        const uint32_t s = T[row][yp][xp];
+        const uint32_t nL = (xp > 0) ? T[row][yp][xp > 0 ? xp - 1 : 0] : xn[dy];
+        const uint32_t nR = (xp < 3) ? T[row][yp][xp < 3 ? xp + 1 : 3] : xn[dy];
+        const uint32_t nU = (yp > 0) ? T[row][yp > 0 ? yp - 1 : 0][xp] : yn[dx];
+        const uint32_t nD = (yp < 3) ? T[row][yp < 3 ? yp + 1 : 3][xp] : yn[dx];
+        const uint32_t v = ((kPar + xp + yp) & 1) ? ~s : s;   // bit of a higher neighbour
+        const uint32_t hL = ~(nL ^ v), hR = ~(nR ^ v), hU = ~(nU ^ v), hD = ~(nD ^ v);
+        fmin[dy][dx] = sel[dy][dx] & hL & hR & hU & hD;                       // local minimum
+        fmax[dy][dx] = kGeneral ? (sel[dy][dx] & ~hL & ~hR & ~hU & ~hD) : 0u;  // local maximum
+      }
+    if (kGeneral) {
+      uint32_t AP, AQ;
+      acceptance<kSK>(P, tc, CR * lane + row, r, fmin[0][0] | fmin[0][1] | fmin[1][0] | fmin[1][1],
+                 fmax[0][0] | fmax[0][1] | fmax[1][0] | fmax[1][1], AP, AQ);
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) { fmin[dy][dx] &= AP; fmax[dy][dx] &= AQ; }
+    }
+    if (kTrack && CR * lane + row == tc.cyo) {
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx)
+          if ((uint32_t)(x0 + dx) == tc.xo && (uint32_t)(y0 + dy) == tc.yo)
+            dh += 2 * (int)((fmin[dy][dx] >> tc.co) & 1u) - 2 * (int)((fmax[dy][dx] >> tc.co) & 1u);
+    }
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-      for (int dx = 0; dx < 2; ++dx)
-        if ((uint32_t)(x0 + dx) == tc.xo && (uint32_t)(y0 + dy) == tc.yo)
-          dh += 2 * (int)((fmin[dy][dx] >> tc.co) & 1u) - 2 * (int)((fmax[dy][dx] >> tc.co) & 1u);
+      for (int dx = 0; dx < 2; ++dx) T[row][y0 + dy][x0 + dx] ^= fmin[dy][dx] | fmax[dy][dx];
   }
-#pragma unroll
-  for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-    for (int dx = 0; dx < 2; ++dx) T[y0 + dy][x0 + dx] ^= fmin[dy][dx] | fmax[dy][dx];
 }
 
-template <bool kGeneral, int kPar, bool kTrack>
-__device__ __forceinline__ void one_round(uint32_t (&T)[4][4], uint32_t Xi, uint32_t Yi,
-                                          const uint32_t (&hx)[4], const uint32_t (&hy)[4],
-                                          const SweepParams& P, const TileCtx& tc, uint32_t lane,
-                                          uint32_t r, int& dh) {
+template <bool kGeneral, int kPar, bool kTrack, int CR, bool kSK>
+__device__ __forceinline__ void one_round(uint32_t (&T)[CR][4][4], const uint32_t (&Xi)[CR],
+                                          const uint32_t (&Yi)[CR], const uint32_t (&hx)[CR][4],
+                                          const uint32_t (&hy)[4], const SweepParams& P,
+                                          const TileCtx& tc, uint32_t lane, uint32_t r, int& dh) {
   switch ((tc.setw >> (2u * r)) & 3u) {
-    case 0: quad_round<0, 0, kGeneral, kPar, kTrack>(T, Xi, Yi, hx, hy, P, tc, lane, r, dh); break;
-    case 1: quad_round<1, 0, kGeneral, kPar, kTrack>(T, Xi, Yi, hx, hy, P, tc, lane, r, dh); break;
-    case 2: quad_round<0, 1, kGeneral, kPar, kTrack>(T, Xi, Yi, hx, hy, P, tc, lane, r, dh); break;
-    default: quad_round<1, 1, kGeneral, kPar, kTrack>(T, Xi, Yi, hx, hy, P, tc, lane, r, dh); break;
+    case 0: quad_round<0, 0, kGeneral, kPar, kTrack, CR, kSK>(T, Xi, Yi, hx, hy, P, tc, lane, r, dh); break;
+    case 1: quad_round<1, 0, kGeneral, kPar, kTrack, CR, kSK>(T, Xi, Yi, hx, hy, P, tc, lane, r, dh); break;
+    case 2: quad_round<0, 1, kGeneral, kPar, kTrack, CR, kSK>(T, Xi, Yi, hx, hy, P, tc, lane, r, dh); break;
+    default: quad_round<1, 1, kGeneral, kPar, kTrack, CR, kSK>(T, Xi, Yi, hx, hy, P, tc, lane, r, dh); break;
   }
 }
 
-// The 16 single-hit rounds of one tile, two rounds per Philox block of positions.
-template <bool kGeneral, int kPar, bool kTrack>
-__device__ __forceinline__ void tile_rounds(uint32_t (&T)[4][4], const uint32_t (&hx)[4],
-                                         const uint32_t (&hy)[4], const SweepParams& P,
-                                         const TileCtx& tc, uint32_t lane, int& dh) {
+// The 16 single-hit rounds of one tile, two rounds per Philox block of
+// positions of each cell row (counter: cell row cy = CR*lane + r, round pair).
+template <bool kGeneral, int kPar, bool kTrack, int CR, bool kSK>
+__device__ __forceinline__ void tile_rounds(uint32_t (&T)[CR][4][4], const uint32_t (&hx)[CR][4],
+                                            const uint32_t (&hy)[4], const SweepParams& P,
+                                            const TileCtx& tc, uint32_t lane, int& dh) {
 #pragma unroll 1
   for (uint32_t rp = 0; rp < kRounds / 2; ++rp) {
-    const uint4 pos = philox((kTagPos << 28) | (lane << 3) | rp, tc.tid, tc.s, P.sample, P.k0, P.k1);
-    one_round<kGeneral, kPar, kTrack>(T, pos.x, pos.y, hx, hy, P, tc, lane, 2u * rp, dh);
-    one_round<kGeneral, kPar, kTrack>(T, pos.z, pos.w, hx, hy, P, tc, lane, 2u * rp + 1u, dh);
+    uint32_t X0[CR], Y0[CR], X1[CR], Y1[CR];
+#pragma unroll
+    for (int row = 0; row < CR; ++row) {
+      const uint4 pos = draw<kSK>(P, tc, (kTagPos << 28) | ((CR * lane + row) << 3) | rp);
+      X0[row] = pos.x; Y0[row] = pos.y; X1[row] = pos.z; Y1[row] = pos.w;
+    }
+    one_round<kGeneral, kPar, kTrack, CR, kSK>(T, X0, Y0, hx, hy, P, tc, lane, 2u * rp, dh);
+    one_round<kGeneral, kPar, kTrack, CR, kSK>(T, X1, Y1, hx, hy, P, tc, lane, 2u * rp + 1u, dh);
   }
+}
+
+// One cell row per lane (128 x 128 tiles), registers as T[y'][x'], hx[y'].
+template <bool kGeneral, int kPar, bool kTrack>
+__device__ __forceinline__ void tile_rounds(uint32_t (&T)[4][4], const uint32_t (&hx)[4],
+                                            const uint32_t (&hy)[4], const SweepParams& P,
+                                            const TileCtx& tc, uint32_t lane, int& dh) {
+  tile_rounds<kGeneral, kPar, kTrack, 1, false>(reinterpret_cast<uint32_t(&)[1][4][4]>(T),
+                                         reinterpret_cast<const uint32_t(&)[1][4]>(hx), hy, P, tc,
+                                         lane, dh);
 }
 
 }  // namespace rounds

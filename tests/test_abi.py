@@ -42,10 +42,14 @@ def test_invalid_arguments_rejected_without_device(lib):
     for L, p, q in bad:
         assert lib.kpz_init(ctypes.byref(c), L, p, q, 1, 0, 0, None) == KPZ_EINVAL
     assert lib.kpz_init(ctypes.byref(c), 256, 1.0, 0.0, 1, 0, 1, None) == KPZ_EINVAL  # init != flat
-    for field, val in [("bx", 64), ("by", 256), ("run", 3), ("run", 4), ("warps_per_cta", 9)]:
+    for field, val in [("bx", 64), ("bx", 256), ("by", 64), ("by", 512), ("run", 3), ("run", 4),
+                       ("warps_per_cta", 9)]:
         o = kpz_opts()
         setattr(o, field, val)
         assert lib.kpz_init(ctypes.byref(c), 256, 1.0, 0.0, 1, 0, 0, ctypes.byref(o)) == KPZ_EINVAL
+    o = kpz_opts()
+    o.by = 256   # 128 x 256 tiles need L >= 256
+    assert lib.kpz_init(ctypes.byref(c), 128, 1.0, 0.0, 1, 0, 0, ctypes.byref(o)) == KPZ_EINVAL
     assert lib.kpz_device_bytes(100) == 0
     assert lib.kpz_device_bytes(256) >= 256 * 256 // 4
     assert lib.kpz_run(None, 1) == KPZ_EINVAL

@@ -147,3 +147,44 @@ def test_rerun_is_deterministic(eng):
         lat.run(10)
         outs.append((lat.slopes(), lat.roughness()))
     assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
+
+
+# 128 x 256 tiles (two cell rows per lane): the same schedule with By = 256.
+CASES_TALL = [
+    (256, 1.0, 0.0, 1, 0, 6),        # one tile row: the tile wraps onto itself in y
+    (512, 1.0, 0.0, 2, 0, 6),
+    (512, 0.95, 0.05, 3, 1, 5),
+    (1024, 0.6, 0.3, 77, 5, 4),
+    (512, 0.0, 1.0, 5, 2, 4),
+]
+
+
+@pytest.mark.parametrize("L,p,q,seed,sample,n", CASES_TALL)
+def test_tall_tiles_bit_exact(eng, L, p, q, seed, sample, n):
+    lat = eng.Lattice(L, p, q, seed=seed, sample=sample, tile_y=2 * TILE)
+    st = O.State.flat(L)
+    for k in range(n):
+        lat.run(1)
+        st.sweep(TILE, 2 * TILE, p, q, seed, sample)
+        _same(lat, st, f"L={L} p={p} q={q} By=256 after sweep {k + 1}")
+
+
+def test_tall_tiles_knobs_and_resume(eng):
+    ref = None
+    for run in (1, 4, 8):
+        for wpc in (1, 2, 4):
+            lat = eng.Lattice(2048, 0.9, 0.1, seed=12, run=run, warps_per_cta=wpc, tile_y=2 * TILE)
+            lat.run(3)
+            w = lat.slopes()
+            if ref is None:
+                ref = (w, lat.roughness())
+            else:
+                assert np.array_equal(w, ref[0]), (run, wpc)
+                assert lat.roughness() == ref[1]
+    st = O.State.flat(2048).run(3, TILE, 2 * TILE, 0.9, 0.1, 12, 0)
+    assert np.array_equal(ref[0], st.packed())
+    b = eng.Lattice(2048, 0.9, 0.1, seed=12, tile_y=2 * TILE)
+    b.set_slopes(ref[0], h00=ref[1]["h00"], t=3)
+    b.run(1)
+    st.sweep(TILE, 2 * TILE, 0.9, 0.1, 12, 0)
+    _same(b, st, "resume with By=256")
