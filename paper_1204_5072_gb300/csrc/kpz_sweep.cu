@@ -157,10 +157,22 @@ __device__ __forceinline__ void sweep_run(const SweepParams& P, WarpStage<CR>& w
   tc.last_lane = last_lane;
   const uint32_t vo = (0u - Y0) & (L - 1u);
 
+  // Quadrant sets: on the p = 1 path lane l draws the set of tile t0 + l
+  // (t0 = t & ~31) and the warp broadcasts it, one draw per 32 tiles.
+  uint32_t set_lane = 0;
 #pragma unroll 1
   for (uint32_t t = 0; t < n; ++t) {
-    tc.tid = ty * P.ntx + tx0 + t;
-    tc.setw = rounds::draw<!kGeneral>(P, tc, kTagSet << 28).x;
+    if (kGeneral) {
+      tc.tid = ty * P.ntx + tx0 + t;
+      tc.setw = philox(kTagSet << 28, tc.tid, s, P.sample, P.k0, P.k1).x;
+    } else {
+      if ((t & 31u) == 0u) {
+        tc.tid = ty * P.ntx + tx0 + t + lane;
+        set_lane = philox_sk(kTagSet << 28, tc.tid, s, P.sample, rk).x;
+      }
+      tc.tid = ty * P.ntx + tx0 + t;
+      tc.setw = __shfl_sync(kFull, set_lane, t & 31u);
+    }
     const uint32_t uo = (0u - ((X0 + t * kTile) & (L - 1u))) & (L - 1u);
     tc.track = (uo < kTile) && (vo < kTileY);
     tc.xo = uo & 3u; tc.co = uo >> 2; tc.yo = vo & 3u; tc.cyo = vo >> 2;
