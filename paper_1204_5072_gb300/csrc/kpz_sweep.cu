@@ -52,6 +52,15 @@ __device__ __forceinline__ void cp_async4(uint32_t* smem, const uint32_t* gmem) 
   const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
+// The same copy, issued only where pred holds (no branch).
+__device__ __forceinline__ void cp_async4_if(bool pred, uint32_t* smem, const uint32_t* gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %0, 0;\n @p cp.async.ca.shared.global [%1], [%2], 4;\n}\n" ::"r"(
+          (uint32_t)pred),
+      "r"(sa), "l"(gmem)
+      : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
@@ -115,7 +124,7 @@ __device__ __forceinline__ void sweep_run(const SweepParams& P, WarpStage<CR>& w
 #pragma unroll
         for (uint32_t yq = 0; yq < 4; ++yq)
           cp_async4(&ws.Pf[t & 1u][r][yq * 4 + xq][lane], c + offY[r][yq]);
-      if (last_lane) cp_async4(&ws.Hf[t % 3u][xq], c + offH);
+      cp_async4_if(last_lane, &ws.Hf[t % 3u][xq], c + offH);
     }
     cp_async_commit();
   };
@@ -210,38 +219,59 @@ __device__ __forceinline__ void sweep_run(const SweepParams& P, WarpStage<CR>& w
 
     // Write back block column t and slide the window to tile t+1.
     cp_async_wait();
+    if (!kGeneral && CR == 1 && t != 0u && !last) {
+      // Interior tile: both words of each window row are this run's alone.
 #pragma unroll
-    for (uint32_t xq = 0; xq < 4; ++xq) {
-      const uint32_t sh = shx[xq];
-      const uint32_t low = (1u << sh) - 1u;
-      uint32_t* cl = col(xq, t);
-      uint32_t* cr = col(xq, t + 1u);
+      for (uint32_t xq = 0; xq < 4; ++xq) {
+        const uint32_t sh = shx[xq];
+        const uint32_t low = (1u << sh) - 1u;
+        uint32_t* cl = col(xq, t);
 #pragma unroll
-      for (int r = 0; r < CR; ++r)
+        for (int r = 0; r < CR; ++r)
 #pragma unroll
-        for (uint32_t yq = 0; yq < 4; ++yq) {
-          const uint32_t Tv = T[r][yq][xq], Mv = ws.M[r][yq * 4 + xq][lane];
-          const uint32_t wl = (Mv & low) | (Tv << sh);                    // word t
-          const uint32_t cn = (Mv & ~low) | __funnelshift_l(Tv, 0u, sh);  // word t+1
-          uint32_t* pl = cl + offY[r][yq];
-          if (t == 0u && sh != 0u) {
-            // left word shared with the run to the left: xor in our changes only
-            const uint32_t delta = (Tv ^ ws.Pf[1][r][yq * 4 + xq][lane]) << sh;
-            if (delta) atomicXor(pl, delta);
-          } else {
-            __stcg(pl, wl);
-          }
-          if (last) {
-            if (sh != 0u) {  // right word shared with the run to the right
-              const uint32_t delta = __funnelshift_l(Tv ^ ws.Pf[keep][r][yq * 4 + xq][lane], 0u, sh);
-              if (delta) atomicXor(cr + offY[r][yq], delta);
-            }
-          } else {
-            const uint32_t N = ws.Pf[t & 1u][r][yq * 4 + xq][lane];  // block column t+2
+          for (uint32_t yq = 0; yq < 4; ++yq) {
+            const uint32_t Tv = T[r][yq][xq], Mv = ws.M[r][yq * 4 + xq][lane];
+            __stcg(cl + offY[r][yq], (Mv & low) | (Tv << sh));                // word t
+            const uint32_t cn = (Mv & ~low) | __funnelshift_l(Tv, 0u, sh);    // word t+1
+            const uint32_t N = ws.Pf[t & 1u][r][yq * 4 + xq][lane];           // block column t+2
             T[r][yq][xq] = __funnelshift_r(cn, N, sh);
             ws.M[r][yq * 4 + xq][lane] = (cn & low) | (N & ~low);
           }
-        }
+      }
+    } else {
+#pragma unroll
+      for (uint32_t xq = 0; xq < 4; ++xq) {
+        const uint32_t sh = shx[xq];
+        const uint32_t low = (1u << sh) - 1u;
+        uint32_t* cl = col(xq, t);
+        uint32_t* cr = col(xq, t + 1u);
+#pragma unroll
+        for (int r = 0; r < CR; ++r)
+#pragma unroll
+          for (uint32_t yq = 0; yq < 4; ++yq) {
+            const uint32_t Tv = T[r][yq][xq], Mv = ws.M[r][yq * 4 + xq][lane];
+            const uint32_t wl = (Mv & low) | (Tv << sh);                    // word t
+            const uint32_t cn = (Mv & ~low) | __funnelshift_l(Tv, 0u, sh);  // word t+1
+            uint32_t* pl = cl + offY[r][yq];
+            if (t == 0u && sh != 0u) {
+              // left word shared with the run to the left: xor in our changes only
+              const uint32_t delta = (Tv ^ ws.Pf[1][r][yq * 4 + xq][lane]) << sh;
+              if (delta) atomicXor(pl, delta);
+            } else {
+              __stcg(pl, wl);
+            }
+            if (last) {
+              if (sh != 0u) {  // right word shared with the run to the right
+                const uint32_t delta = __funnelshift_l(Tv ^ ws.Pf[keep][r][yq * 4 + xq][lane], 0u, sh);
+                if (delta) atomicXor(cr + offY[r][yq], delta);
+              }
+            } else {
+              const uint32_t N = ws.Pf[t & 1u][r][yq * 4 + xq][lane];  // block column t+2
+              T[r][yq][xq] = __funnelshift_r(cn, N, sh);
+              ws.M[r][yq * 4 + xq][lane] = (cn & low) | (N & ~low);
+            }
+          }
+      }
     }
     if (t + 2u < n) prefetch(t + 3u);   // for the end of tile t+1
   }
