@@ -24,6 +24,7 @@ import subprocess
 import sys
 import threading
 import time
+import warnings
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -68,14 +69,22 @@ K_ALG_ALU = 20 / 64 + 22 / 32 + 64 / 512
 ALU_LANES_PER_SM = 64   # integer logic pipe: 16 lanes per SM sub-partition per clock
 
 
+# Files the sweep kernel is compiled from (their hash ties a profile to the source).
+SWEEP_SOURCES = ("kpz_sweep.cu", "kpz_rounds.cuh", "kpz_common.cuh", "kpz_internal.h")
+
+
+def sweep_source_sha():
+    import hashlib
+    src = b"".join(open(os.path.join(ROOT, "paper_1204_5072_gb300", "csrc", f), "rb").read()
+                   for f in SWEEP_SOURCES)
+    return hashlib.sha256(src).hexdigest()[:16]
+
+
 def measured_traffic(L):
     """DRAM bytes per sweep launch from the committed ncu summary, if it was
     taken on this size and on the current kernel source; else None."""
-    import hashlib
     try:
-        src = b"".join(open(os.path.join(ROOT, "paper_1204_5072_gb300", "csrc", f), "rb").read()
-                       for f in ("kpz_sweep.cu", "kpz_common.cuh"))
-        sha = hashlib.sha256(src).hexdigest()[:16]
+        sha = sweep_source_sha()
         txt = open(os.path.join(ROOT, "profiles", "sweep_kernel_L65536.md")).read()
         fields = dict(ln.split(": ", 1) for ln in txt.splitlines() if ": " in ln and ln[:1].isalpha())
         if L == 65536 and fields.get("source_sha256") == sha:
@@ -269,7 +278,8 @@ def surrogate_bench(eng):
         out = {}
         for (L, p) in pairs:
             rows = [i for i, sp in enumerate(specs) if sp[0] == L and sp[1] == p]
-            with np.errstate(invalid="ignore"):
+            with warnings.catch_warnings():   # times past every run's end are all-NaN columns
+                warnings.simplefilter("ignore", RuntimeWarning)
                 out[(L, p)] = np.nanmean(w[rows], axis=0)
         return t, out
 

@@ -176,7 +176,7 @@ kpz_status kpz_init(kpz_ctx** out, uint32_t L, double p, double q, uint64_t seed
   ctx->sample = sample;
   ctx->tile_y = o.by ? o.by : kTile;
   ctx->run = o.run ? o.run : std::min(8u, ntx);   // tiles per work-queue chunk
-  ctx->wpc = o.warps_per_cta ? o.warps_per_cta : 4u;
+  ctx->wpc = o.warps_per_cta ? o.warps_per_cta : 8u;
   ctx->stream = (cudaStream_t)o.stream;
   if (o.dev_buf) {
     ctx->buf = o.dev_buf;

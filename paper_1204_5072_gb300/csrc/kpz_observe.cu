@@ -8,6 +8,8 @@
 //   h(0,j) = sum_{k<j} sigma_y(0,k),
 // then along each row, h(i,j) = h(0,j) + sum_{l<i} sigma_x(l,j); on a valid
 // (curl-free) surface this equals any other path sum.
+#include <algorithm>
+
 #include "kpz_internal.h"
 
 namespace kpz {
@@ -122,18 +124,38 @@ __global__ void import_rows_kernel(uint32_t* __restrict__ lat, Geometry g, uint3
   }
 }
 
-// h(0,j) for all rows j, gauge h(0,0) = 0: one block, chunked sums + block scan.
-__global__ void col0_kernel(const uint32_t* __restrict__ lat, Geometry g, int32_t* __restrict__ col0) {
-  __shared__ int32_t part[1024];
+// h(0,j) for all rows j, gauge h(0,0) = 0: one block; thread t owns rows
+// [t chunk, (t+1) chunk) in pieces of 32. A piece's 32 bits b(0, j) are loaded
+// at once into a mask; its steps sigma_y(0, j) = +1 where b(0,j) ^ b(0,j+1)
+// equals the parity of j + par, so the piece's height change is
+// 2 popc(E) - 32; a block scan of the chunk sums gives each chunk's start.
+constexpr uint32_t kCol0Threads = 1024;
+
+__global__ void __launch_bounds__(kCol0Threads) col0_kernel(const uint32_t* __restrict__ lat, Geometry g,
+                                                           int32_t* __restrict__ col0) {
+  __shared__ int32_t part[kCol0Threads];
   const uint32_t nt = blockDim.x, t = threadIdx.x;
-  const uint32_t chunk = (g.L + nt - 1) / nt;
-  const uint32_t j0 = min(g.L, t * chunk), j1 = min(g.L, j0 + chunk);
-  auto step = [&](uint32_t j) -> int32_t {  // sigma_y(0, j)
-    const uint32_t b = site_bit(lat, g, 0, j), bn = site_bit(lat, g, 0, (j + 1u) & (g.L - 1u));
-    return ((b ^ bn) == ((j + g.par) & 1u)) ? 1 : -1;
+  const uint32_t chunk = g.L / nt;                 // multiple of 32
+  const uint32_t j0 = t * chunk, pieces = chunk / 32u;
+  const uint32_t parpat = ((g.par & 1u) ? 0x55555555u : 0xAAAAAAAAu);  // bit i: (j0+32p+i+par) odd
+  auto piece_steps = [&](uint32_t jp) -> uint32_t {   // E bits of rows jp .. jp+31
+    // Rows jp + 4r + y4 (r < 8): words R0 + r of plane (y4, 0), R0 = jp/4 a
+    // multiple of 8, read as two 16-byte vectors per plane.
+    uint32_t b = 0;
+#pragma unroll
+    for (uint32_t y4 = 0; y4 < 4u; ++y4) {
+      const uint4* v = reinterpret_cast<const uint4*>(lat + g.word(0, plane(y4, 0), jp >> 2));
+      const uint4 lo = __ldcg(v), hi = __ldcg(v + 1);
+      const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+      for (uint32_t r = 0; r < 8u; ++r) b |= (w[r] & 1u) << (4u * r + y4);
+    }
+    const uint32_t jn = (jp + 32u) & (g.L - 1u);
+    const uint32_t bn = __ldcg(lat + g.word(0, plane(jn & 3u, 0), jn >> 2)) & 1u;
+    return ~(b ^ ((b >> 1) | (bn << 31)) ^ parpat);
   };
   int32_t sum = 0;
-  for (uint32_t j = j0; j < j1; ++j) sum += step(j);
+  for (uint32_t p = 0; p < pieces; ++p) sum += 2 * __popc(piece_steps(j0 + 32u * p)) - 32;
   part[t] = sum;
   __syncthreads();
   for (uint32_t off = 1; off < nt; off <<= 1) {   // inclusive Hillis-Steele scan
@@ -143,9 +165,14 @@ __global__ void col0_kernel(const uint32_t* __restrict__ lat, Geometry g, int32_
     __syncthreads();
   }
   int32_t h = (t == 0) ? 0 : part[t - 1];
-  for (uint32_t j = j0; j < j1; ++j) {
-    col0[j] = h;
-    h += step(j);
+  for (uint32_t p = 0; p < pieces; ++p) {
+    const uint32_t E = piece_steps(j0 + 32u * p);
+    int32_t* o = col0 + j0 + 32u * p;
+#pragma unroll 8
+    for (uint32_t i = 0; i < 32u; ++i) {
+      o[i] = h;
+      h += ((E >> i) & 1u) ? 1 : -1;
+    }
   }
 }
 
@@ -162,54 +189,128 @@ __device__ __forceinline__ void sigma_x_planes(const uint32_t (&P)[4], uint32_t 
 }
 
 // Exact S1 = sum h and S2 = sum h^2 (eq. Wdef). Lane <-> row j = 4R + y4 with
-// consecutive R per warp (coalesced plane loads); each 128-site block is
-// summed relative to its first site in 32-bit, then promoted to 64-bit.
-__global__ void roughness_kernel(const uint32_t* __restrict__ lat, Geometry g,
-                                 const int32_t* __restrict__ col0,
-                                 unsigned long long* __restrict__ acc) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const uint32_t y4 = gw & 3u, R = (gw >> 2) * 32u + lane;
-  long long s1 = 0;
-  unsigned long long s2 = 0;
-  if (R < g.NR) {
-    const uint32_t j = 4u * R + y4;
-    long long H = col0[j];
-    uint32_t P[4];
+// consecutive R per warp (coalesced plane loads). A 128-site block is cut into
+// 16 runs of 8 consecutive sites; for each run a table gives, from its 8 step
+// bits, the height change D and the sums A1 = sum r, A2 = sum r^2 of the
+// heights r relative to its first site, so a run starting at height h adds
+// 8h + A1 to S1 and 8h^2 + 2h A1 + A2 to S2. Sums are relative to the block's
+// first site in 32-bit, then promoted to 64-bit.
+//
+// Run bytes: bits (0, 1) = steps of sites 4c and 4c+4 of plane 0 at cells
+// c, c+1, bits (2, 3) plane 1, (4, 5) plane 2, (6, 7) plane 3; in x order the
+// sites are bits 0, 2, 4, 6, 1, 3, 5, 7.
+constexpr uint32_t kRunTable = 256;
+
+// Table entry of run byte b: A2 | (A1 + 28) << 8 | (D + 8) << 16.
+__device__ __forceinline__ uint32_t run_entry(uint32_t b) {
+  int32_t r = 0, a1 = 0, a2 = 0;
 #pragma unroll
-    for (uint32_t x4 = 0; x4 < 4; ++x4) P[x4] = __ldcg(lat + g.word(0, plane(y4, x4), R));
-    for (uint32_t K = 0; K < g.NB; ++K) {
-      uint32_t Pn[4];
-      const uint32_t Kn = (K + 1u) & (g.NB - 1u);
-#pragma unroll
-      for (uint32_t x4 = 0; x4 < 4; ++x4) Pn[x4] = __ldcg(lat + g.word(Kn, plane(y4, x4), R));
-      uint32_t S[4];
-      sigma_x_planes(P, Pn[0] & 1u, j, g.par, S);
-      int32_t h = 0, a1 = 0, a2 = 0;
+  for (int k = 0; k < 8; ++k) {
+    const uint32_t bit = (b >> ((k & 3) * 2 + (k >> 2))) & 1u;
+    a1 += r;
+    a2 += r * r;
+    r += 2 * (int32_t)bit - 1;
+  }
+  return (uint32_t)a2 | ((uint32_t)(a1 + 28) << 8) | ((uint32_t)(r + 8) << 16);
+}
+
+// The 16 run bytes of a block from its step planes S: u[q] byte m holds the
+// run of cells 8m + 2q' .. 8m + 2q' + 1 with q' = (0, 2, 1, 3)[q].
+__device__ __forceinline__ void run_bytes(const uint32_t (&S)[4], uint32_t (&u)[4]) {
+  const uint32_t t01 = (S[0] & 0x33333333u) | ((S[1] << 2) & 0xCCCCCCCCu);   // cells 4k, 4k+1
+  const uint32_t t01b = ((S[0] >> 2) & 0x33333333u) | (S[1] & 0xCCCCCCCCu);  // cells 4k+2, 4k+3
+  const uint32_t t23 = (S[2] & 0x33333333u) | ((S[3] << 2) & 0xCCCCCCCCu);
+  const uint32_t t23b = ((S[2] >> 2) & 0x33333333u) | (S[3] & 0xCCCCCCCCu);
+  u[0] = (t01 & 0x0F0F0F0Fu) | ((t23 << 4) & 0xF0F0F0F0u);    // cells 8m, 8m+1
+  u[1] = (t01b & 0x0F0F0F0Fu) | ((t23b << 4) & 0xF0F0F0F0u);  // cells 8m+2, 8m+3
+  u[2] = ((t01 >> 4) & 0x0F0F0F0Fu) | (t23 & 0xF0F0F0F0u);    // cells 8m+4, 8m+5
+  u[3] = ((t01b >> 4) & 0x0F0F0F0Fu) | (t23b & 0xF0F0F0F0u);  // cells 8m+6, 8m+7
+}
+
+// Work split: warp -> (y4, 8 consecutive storage rows R); lane -> row R + (lane & 7)
+// and segment q = lane >> 3 of kSegs block columns each; a segment's start
+// height is col0 plus the height changes of the segments before it (a scan
+// over the 4 lanes of the row).
+constexpr uint32_t kRowsPerWarp = 8, kSegs = 4;
+
+__global__ void __launch_bounds__(256) roughness_kernel(const uint32_t* __restrict__ lat, Geometry g,
+                                                        const int32_t* __restrict__ col0,
+                                                        unsigned long long* __restrict__ acc) {
+  // Run table, one copy per lane (entry e of lane l at e*32 + l: no bank conflicts).
+  __shared__ uint32_t tab[kRunTable * 32];
+  for (uint32_t e = threadIdx.x; e < kRunTable; e += blockDim.x) {
+    const uint32_t v = run_entry(e);
 #pragma unroll 8
-      for (uint32_t c = 0; c < 32; ++c)
+    for (uint32_t l = 0; l < 32; ++l) tab[e * 32u + l] = v;
+  }
+  __syncthreads();
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t* tl = tab + lane;
+  const uint32_t gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const uint32_t y4 = gw & 3u, R = (gw >> 2) * kRowsPerWarp + (lane & (kRowsPerWarp - 1u));
+  const uint32_t q = lane / kRowsPerWarp;
+  const uint32_t seg = (g.NB + kSegs - 1u) / kSegs;               // block columns per segment
+  const uint32_t K0 = q * seg, K1 = min(g.NB, K0 + seg);
+  const bool active = R < g.NR && K0 < K1;
+  long long s1 = 0, s2 = 0, dH = 0;   // relative to the segment's first site
+  if (active) {
+    uint32_t P[4], Pn[4];
 #pragma unroll
-        for (uint32_t x4 = 0; x4 < 4; ++x4) {
-          a1 += h;
-          a2 += h * h;
-          h += 2 * (int32_t)((S[x4] >> c) & 1u) - 1;
-        }
-      s1 += 128 * H + a1;
-      s2 += (unsigned long long)(128 * H * H + 2 * H * (long long)a1 + (long long)a2);
-      H += h;
-#pragma unroll
-      for (uint32_t x4 = 0; x4 < 4; ++x4) P[x4] = Pn[x4];
+    for (uint32_t x4 = 0; x4 < 4; ++x4) {
+      P[x4] = __ldcg(lat + g.word(K0, plane(y4, x4), R));
+      Pn[x4] = __ldcg(lat + g.word((K0 + 1u) & (g.NB - 1u), plane(y4, x4), R));
     }
+    const uint32_t j = 4u * R + y4;
+    for (uint32_t K = K0; K < K1; ++K) {
+      uint32_t Pnn[4];   // two blocks ahead
+      const uint32_t K2 = (K + 2u) & (g.NB - 1u);
+#pragma unroll
+      for (uint32_t x4 = 0; x4 < 4; ++x4) Pnn[x4] = __ldcg(lat + g.word(K2, plane(y4, x4), R));
+      uint32_t S[4], u[4];
+      sigma_x_planes(P, Pn[0] & 1u, j, g.par, S);
+      run_bytes(S, u);
+      int32_t h = 0, a1 = 0, a2 = 0;
+#pragma unroll
+      for (uint32_t m = 0; m < 4; ++m)
+#pragma unroll
+        for (uint32_t qq = 0; qq < 4; ++qq) {
+          const uint32_t w = tl[((u[qq] >> (8u * m)) & 0xFFu) * 32u];
+          const int32_t A2 = (int32_t)(w & 0xFFu), A1 = (int32_t)((w >> 8) & 0xFFu) - 28;
+          a1 += 8 * h + A1;
+          a2 += h * (8 * h + 2 * A1) + A2;
+          h += (int32_t)(w >> 16) - 8;
+        }
+      s1 += 128 * dH + a1;
+      s2 += 128 * dH * dH + 2 * dH * (long long)a1 + (long long)a2;
+      dH += h;
+#pragma unroll
+      for (uint32_t x4 = 0; x4 < 4; ++x4) { P[x4] = Pn[x4]; Pn[x4] = Pnn[x4]; }
+    }
+  }
+  // Start height of this segment: col0[j] + height changes of the row's earlier segments.
+  long long pre = dH;
+#pragma unroll
+  for (uint32_t d = kRowsPerWarp; d < 32u; d <<= 1) {
+    const long long v = __shfl_up_sync(0xffffffffu, pre, d);
+    if (lane >= d) pre += v;
+  }
+  long long t1 = 0;
+  unsigned long long t2 = 0;
+  if (active) {
+    const long long H0 = (long long)col0[4u * R + y4] + (pre - dH);
+    const long long n = 128ll * (K1 - K0);
+    t1 = n * H0 + s1;
+    t2 = (unsigned long long)(n * H0 * H0 + 2 * H0 * s1 + s2);
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
-    s1 += __shfl_xor_sync(0xffffffffu, s1, off);
-    s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+    t1 += __shfl_xor_sync(0xffffffffu, t1, off);
+    t2 += __shfl_xor_sync(0xffffffffu, t2, off);
   }
-  if (lane == 0 && (s1 != 0 || s2 != 0)) {
-    atomicAdd(&acc[0], (unsigned long long)s1);
-    const unsigned long long old = atomicAdd(&acc[1], s2);
-    if (old + s2 < old) atomicAdd(&acc[2], 1ull);
+  if (lane == 0 && (t1 != 0 || t2 != 0)) {
+    atomicAdd(&acc[0], (unsigned long long)t1);
+    const unsigned long long old = atomicAdd(&acc[1], t2);
+    if (old + t2 < old) atomicAdd(&acc[2], 1ull);
   }
 }
 
@@ -270,7 +371,7 @@ cudaError_t launch_import_packed(uint32_t* lat, Geometry g, uint32_t j0, uint32_
 }
 
 cudaError_t launch_col0(const uint32_t* lat, Geometry g, int32_t* col0, cudaStream_t st) {
-  col0_kernel<<<1, 1024, 0, st>>>(lat, g, col0);
+  col0_kernel<<<1, std::min(kCol0Threads, g.L / 32u), 0, st>>>(lat, g, col0);
   count_launch();
   return cudaGetLastError();
 }
@@ -279,9 +380,9 @@ cudaError_t launch_roughness(const uint32_t* lat, Geometry g, int32_t* col0,
                              unsigned long long* acc, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(acc, 0, 3 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
-  col0_kernel<<<1, 1024, 0, st>>>(lat, g, col0);
+  col0_kernel<<<1, std::min(kCol0Threads, g.L / 32u), 0, st>>>(lat, g, col0);
   count_launch();
-  const uint32_t warps = 4u * ((g.NR + 31u) / 32u);
+  const uint32_t warps = 4u * ((g.NR + kRowsPerWarp - 1u) / kRowsPerWarp);
   const uint32_t wpc = 8;
   roughness_kernel<<<(warps + wpc - 1) / wpc, wpc * 32, 0, st>>>(lat, g, col0, acc);
   count_launch();
