@@ -405,6 +405,15 @@ def main():
                 "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
                         "frac": hbm_achieved / hbm_peak, "alg_bytes_per_launch": alg_bytes,
                         "peak_source": f"{peak_kind} hbm_gbs"}}
+    # The derived ALU peak checked by the engine's own LOP3 throughput probe
+    # (outside the timed region).
+    try:
+        probe = eng._lib.alu_peak()
+        roofline["peak_probe"] = {"value": probe["lane_ops_per_s"] / 1e12, "unit": "Top/s",
+                                  "of_derived": probe["lane_ops_per_s"] / 1e12 / alu_peak,
+                                  "source": "kpz_alu_peak: one wave of independent LOP3 chains"}
+    except Exception as exc:   # report, do not hide
+        roofline["peak_probe"] = {"error": str(exc)}
 
     # End to end through the C ABI with host buffers: upload the start state
     # from pinned memory, run the job with W^2 sampling, read the final lattice.

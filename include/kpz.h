@@ -51,7 +51,9 @@ typedef enum {
     KPZ_ETIMEOUT = 4, /* a bounded device-side wait gave up                   */
     KPZ_ESTATE = 5,   /* context poisoned by an earlier error                 */
     KPZ_ENODEV = 6,   /* no usable CUDA device                                */
-    KPZ_ERANGE = 7    /* size beyond the fixed scratch of kpz_roughness_static */
+    KPZ_ERANGE = 7,   /* size beyond the fixed scratch of kpz_roughness_static */
+    KPZ_ECKPT = 8     /* checkpoint file unreadable, unwritable, truncated,
+                         not a checkpoint, or its checksum does not match    */
 } kpz_status;
 
 typedef struct kpz_ctx kpz_ctx;
@@ -66,7 +68,7 @@ typedef struct {
                              `run` tiles of one tile row from a queue (power of two
                              <= L/128; 0 = min(8, L/128)); execution only, it does
                              not change the result                                 */
-    uint32_t warps_per_cta; /* 1..8, 0 = 4; execution only                         */
+    uint32_t warps_per_cta; /* 1..8, 0 = 8; execution only                         */
     void* stream;         /* cudaStream_t to queue work on (NULL = default stream)  */
     void* dev_buf;        /* optional caller-owned device memory for the lattice and
                              its scratch; at least kpz_device_bytes(L) bytes,
@@ -128,6 +130,34 @@ kpz_status kpz_slopes(kpz_ctx* ctx, uint32_t* host_out);
  * zero), set the absolute height of site (0,0) to h00 and the sweep counter
  * to t_mcs. Validity is the caller's responsibility. Synchronises.          */
 kpz_status kpz_set_slopes(kpz_ctx* ctx, const uint32_t* host_in, int64_t h00, uint64_t t_mcs);
+
+/* Checkpoints (not in the paper; they let a long run such as the L = 2^16
+ * job stop and resume). kpz_ckpt_save writes the context's whole state to
+ * the file `path` (created or truncated):
+ *   header   "KPZCKPT1", version 1, L, p, q (as given to kpz_init), the
+ *            thresholds Tp, Tq, seed, sample, tile shape (bx, by), the sweep
+ *            counter t_mcs and the absolute height of site (0,0);
+ *   payload  the lattice in the packed exchange format (L*L/16 uint32,
+ *            row-major, as kpz_slopes), written in bands;
+ *   trailer  a 64-bit FNV-1a checksum over the header and payload taken as
+ *            little-endian 64-bit words.
+ * kpz_ckpt_load creates a new context (*out, owned by the caller) from such a
+ * file; opts supplies the execution options (run, warps_per_cta, stream,
+ * dev_buf) as in kpz_init, and its bx, by must be 0 or equal the file's tile
+ * shape. Running the loaded context gives the same lattices, bit for bit, as
+ * the uninterrupted run. Both synchronise. Errors: KPZ_ECKPT for file and
+ * format problems (nothing is created on load), KPZ_EINVAL for null
+ * arguments or conflicting opts, otherwise as kpz_init / kpz_slopes.        */
+kpz_status kpz_ckpt_save(kpz_ctx* ctx, const char* path);
+kpz_status kpz_ckpt_load(kpz_ctx** out, const char* path, const kpz_opts* opts);
+
+/* Throughput probe of the integer logic pipe that bounds the sweep (not in
+ * the paper): one wave of CTAs runs independent chains of three-input XORs
+ * (LOP3) on the current device; *lane_ops_per_s receives the measured rate
+ * in lane operations per second and *kernel_ms (may be NULL) the kernel's
+ * time. Synchronises its own stream. KPZ_EINVAL for a null output,
+ * KPZ_ECUDA if a CUDA call fails.                                            */
+kpz_status kpz_alu_peak(double* lane_ops_per_s, double* kernel_ms);
 
 /* Device pointer of the lattice and its size in bytes, L*L/8 (for callers that
  * keep the lattice resident and time kernels on the context stream). */

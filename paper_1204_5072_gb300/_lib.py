@@ -12,7 +12,8 @@ import numpy as np
 
 from . import build as _build
 
-KPZ_OK, KPZ_EINVAL, KPZ_ENOMEM, KPZ_ECUDA, KPZ_ETIMEOUT, KPZ_ESTATE, KPZ_ENODEV, KPZ_ERANGE = range(8)
+(KPZ_OK, KPZ_EINVAL, KPZ_ENOMEM, KPZ_ECUDA, KPZ_ETIMEOUT, KPZ_ESTATE, KPZ_ENODEV, KPZ_ERANGE,
+ KPZ_ECKPT) = range(9)
 
 
 class KpzError(RuntimeError):
@@ -58,6 +59,10 @@ def load(path: str | None = None):
     L.kpz_slopes.argtypes = [vp, vp]
     L.kpz_set_slopes.argtypes = [vp, vp, c.c_int64, c.c_uint64]
     L.kpz_device_lattice.argtypes = [vp, c.POINTER(vp), c.POINTER(c.c_size_t)]
+    L.kpz_ckpt_save.argtypes = [vp, c.c_char_p]
+    L.kpz_alu_peak.argtypes = [c.POINTER(c.c_double), c.POINTER(c.c_double)]
+    L.kpz_alu_peak.restype = c.c_int
+    L.kpz_ckpt_load.argtypes = [c.POINTER(vp), c.c_char_p, c.POINTER(kpz_opts)]
     L.kpz_roughness_static.argtypes = [vp, c.c_uint32, c.c_uint32, vp, c.POINTER(kpz_rough)]
     L.kpz_roughness_static.restype = c.c_int
     L.kpz_launch_count.argtypes = []
@@ -69,7 +74,7 @@ def load(path: str | None = None):
     L.kpz_last_error.argtypes = [vp]
     L.kpz_last_error.restype = c.c_char_p
     for fn in ("kpz_init", "kpz_reset", "kpz_run", "kpz_roughness", "kpz_heights", "kpz_slopes",
-               "kpz_set_slopes", "kpz_device_lattice"):
+               "kpz_set_slopes", "kpz_device_lattice", "kpz_ckpt_save", "kpz_ckpt_load"):
         getattr(L, fn).restype = c.c_int
     _lib = L
     return L
@@ -89,6 +94,13 @@ def check(st: int, ctx=None):
 def launch_count() -> int:
     """Kernels launched by the engine in this process so far."""
     return int(load().kpz_launch_count())
+
+
+def alu_peak() -> dict:
+    """Measured integer-logic (LOP3) lane operations per second (kpz_alu_peak)."""
+    rate, ms = ctypes.c_double(), ctypes.c_double()
+    check(load().kpz_alu_peak(ctypes.byref(rate), ctypes.byref(ms)))
+    return {"lane_ops_per_s": rate.value, "kernel_ms": ms.value}
 
 
 def _ptr(a: np.ndarray):
@@ -177,6 +189,38 @@ class Lattice:
         w = np.ascontiguousarray(words, np.uint32)
         assert w.size == self.L * self.L // 16
         check(load().kpz_set_slopes(self._ctx, _ptr(w), int(h00), int(t)), self._ctx)
+        return self
+
+    def save(self, path) -> "Lattice":
+        """Write a checkpoint (kpz_ckpt_save): header, packed lattice, checksum."""
+        check(load().kpz_ckpt_save(self._ctx, os.fsencode(path)), self._ctx)
+        return self
+
+    @classmethod
+    def load(cls, path, run: int = 0, warps_per_cta: int = 0, stream=None) -> "Lattice":
+        """A new lattice from a checkpoint (kpz_ckpt_load); L, p, q, seed,
+        sample and tile shape come from the file."""
+        lib = load()
+        o = kpz_opts()
+        o.run, o.warps_per_cta = run, warps_per_cta
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream().cuda_stream
+            except ImportError:
+                pass
+        o.stream = stream or None
+        ctx = ctypes.c_void_p()
+        check(lib.kpz_ckpt_load(ctypes.byref(ctx), os.fsencode(path), ctypes.byref(o)))
+        self = cls.__new__(cls)
+        self._buf = None
+        self._ctx = ctx
+        hd = np.fromfile(path, dtype=np.uint8, count=64)   # header fields of kpz_ckpt_save
+        self.L = int(hd[12:16].view(np.uint32)[0])
+        self.p, self.q = (float(v) for v in hd[16:32].view(np.float64))
+        self.seed = int(hd[40:48].view(np.uint64)[0])
+        self.sample = int(hd[48:52].view(np.uint32)[0])
         return self
 
     def device_lattice(self):

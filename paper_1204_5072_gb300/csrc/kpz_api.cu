@@ -22,6 +22,7 @@ void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxe
 struct kpz_ctx {
   Geometry g{};
   uint32_t Tp = 0, Tq = 0, nlev = 0, sample = 0;
+  double p = 0.0, q = 0.0;             // as given to kpz_init (checkpoint header)
   uint64_t seed = 0;
   uint32_t run = 1, wpc = 8;
   uint32_t tile_y = 128;               // tile height in sites (128 or 256)
@@ -135,6 +136,7 @@ const char* kpz_strerror(kpz_status st) {
     case KPZ_ESTATE: return "context poisoned by an earlier error";
     case KPZ_ENODEV: return "no CUDA device";
     case KPZ_ERANGE: return "lattice larger than the 131072 maximum of the static scratch";
+    case KPZ_ECKPT: return "checkpoint file unreadable, truncated or corrupt";
   }
   return "unknown status";
 }
@@ -169,6 +171,8 @@ kpz_status kpz_init(kpz_ctx** out, uint32_t L, double p, double q, uint64_t seed
   ctx->g.NR = L / 4;
   ctx->g.NB = L / 128;
   ctx->g.par = 0;
+  ctx->p = p;
+  ctx->q = q;
   ctx->Tp = acceptance_threshold(p);
   ctx->Tq = acceptance_threshold(q);
   ctx->nlev = acceptance_levels(ctx->Tp, ctx->Tq);
@@ -321,6 +325,136 @@ kpz_status kpz_set_slopes(kpz_ctx* ctx, const uint32_t* host_in, int64_t h00, ui
   KPZ_CUDA(cudaMemcpyAsync(ctx->t_dev, small, sizeof(small), cudaMemcpyHostToDevice, ctx->stream));
   KPZ_CUDA(cudaStreamSynchronize(ctx->stream));
   ctx->t_host = t_mcs;
+  return KPZ_OK;
+}
+
+namespace {
+
+struct CkptHeader {
+  char magic[8];
+  uint32_t version, L;
+  double p, q;
+  uint32_t Tp, Tq;
+  uint64_t seed;
+  uint32_t sample, bx, by, reserved;
+  uint64_t t_mcs;
+  int64_t h00;
+};
+static_assert(sizeof(CkptHeader) % 8 == 0, "checksum runs over 64-bit words");
+constexpr char kCkptMagic[8] = {'K', 'P', 'Z', 'C', 'K', 'P', 'T', '1'};
+constexpr uint64_t kFnvBasis = 0xcbf29ce484222325ull, kFnvPrime = 0x100000001b3ull;
+
+// FNV-1a over little-endian 64-bit words (n a multiple of 8).
+uint64_t fnv_words(uint64_t h, const void* data, size_t n) {
+  const unsigned char* b = (const unsigned char*)data;
+  for (size_t i = 0; i < n; i += 8) {
+    uint64_t w = 0;
+    for (int k = 7; k >= 0; --k) w = (w << 8) | b[i + k];
+    h = (h ^ w) * kFnvPrime;
+  }
+  return h;
+}
+
+struct File {
+  FILE* f = nullptr;
+  ~File() { if (f) fclose(f); }
+};
+
+}  // namespace
+
+kpz_status kpz_ckpt_save(kpz_ctx* ctx, const char* path) {
+  kpz_status st = enter(ctx);
+  if (st) return st;
+  if (!path) return fail(ctx, KPZ_EINVAL, "null path");
+  const uint32_t L = ctx->g.L;
+  CkptHeader hd{};
+  memcpy(hd.magic, kCkptMagic, 8);
+  hd.version = 1;
+  hd.L = L;
+  hd.p = ctx->p;
+  hd.q = ctx->q;
+  hd.Tp = ctx->Tp;
+  hd.Tq = ctx->Tq;
+  hd.seed = ctx->seed;
+  hd.sample = ctx->sample;
+  hd.bx = kTile;
+  hd.by = ctx->tile_y;
+  unsigned long long small[2];
+  KPZ_CUDA(cudaMemcpyAsync(small, ctx->t_dev, sizeof(small), cudaMemcpyDeviceToHost, ctx->stream));
+  KPZ_CUDA(cudaStreamSynchronize(ctx->stream));
+  hd.t_mcs = small[0];
+  hd.h00 = (int64_t)small[1];
+  File out;
+  out.f = fopen(path, "wb");
+  if (!out.f) return fail(ctx, KPZ_ECKPT, std::string("cannot create ") + path);
+  uint64_t h = fnv_words(kFnvBasis, &hd, sizeof(hd));
+  if (fwrite(&hd, sizeof(hd), 1, out.f) != 1) return fail(ctx, KPZ_ECKPT, "write failed");
+  const size_t row_bytes = (size_t)L / 16 * 4;
+  const uint32_t band = (uint32_t)std::min<size_t>(L, ctx->io_bytes / row_bytes) & ~3u;
+  std::string host((size_t)band * row_bytes, '\0');
+  for (uint32_t j0 = 0; j0 < L; j0 += band) {
+    const uint32_t nr = std::min(band, L - j0);
+    KPZ_CUDA(launch_export_packed(ctx->lat, ctx->g, j0, nr, (uint32_t*)ctx->io, ctx->stream));
+    KPZ_CUDA(cudaMemcpyAsync(&host[0], ctx->io, nr * row_bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    KPZ_CUDA(cudaStreamSynchronize(ctx->stream));
+    h = fnv_words(h, host.data(), nr * row_bytes);
+    if (fwrite(host.data(), 1, nr * row_bytes, out.f) != nr * row_bytes)
+      return fail(ctx, KPZ_ECKPT, "write failed");
+  }
+  if (fwrite(&h, sizeof(h), 1, out.f) != 1 || fflush(out.f) != 0)
+    return fail(ctx, KPZ_ECKPT, "write failed");
+  return KPZ_OK;
+}
+
+kpz_status kpz_ckpt_load(kpz_ctx** out, const char* path, const kpz_opts* opts) {
+  if (!out || !path) return KPZ_EINVAL;
+  *out = nullptr;
+  File in;
+  in.f = fopen(path, "rb");
+  if (!in.f) return KPZ_ECKPT;
+  CkptHeader hd{};
+  if (fread(&hd, sizeof(hd), 1, in.f) != 1 || memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != 1 ||
+      !valid_L(hd.L) || hd.bx != kTile || (hd.by != kTile && hd.by != 2u * kTile) ||
+      acceptance_threshold(hd.p) != hd.Tp || acceptance_threshold(hd.q) != hd.Tq)
+    return KPZ_ECKPT;
+  kpz_opts o{};
+  if (opts) o = *opts;
+  if ((o.bx != 0 && o.bx != hd.bx) || (o.by != 0 && o.by != hd.by)) return KPZ_EINVAL;
+  o.bx = hd.bx;
+  o.by = hd.by;
+  kpz_ctx* ctx = nullptr;
+  kpz_status st = kpz_init(&ctx, hd.L, hd.p, hd.q, hd.seed, hd.sample, 0, &o);
+  if (st) return st;
+  auto bail = [&](kpz_status s) { kpz_free(ctx); return s; };
+  uint64_t h = fnv_words(kFnvBasis, &hd, sizeof(hd));
+  const uint32_t L = hd.L;
+  const size_t row_bytes = (size_t)L / 16 * 4;
+  const uint32_t band = (uint32_t)std::min<size_t>(L, ctx->io_bytes / row_bytes) & ~3u;
+  std::string host((size_t)band * row_bytes, '\0');
+  ctx->g.par = (uint32_t)(hd.h00 & 1);
+  const uint32_t h00_mod4 = (uint32_t)(hd.h00 & 3);
+  if (cudaMemcpyAsync(ctx->hcar, &h00_mod4, sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream) !=
+      cudaSuccess)
+    return bail(KPZ_ECUDA);
+  for (uint32_t j0 = 0; j0 < L; j0 += band) {
+    const uint32_t nr = std::min(band, L - j0);
+    if (fread(&host[0], 1, nr * row_bytes, in.f) != nr * row_bytes) return bail(KPZ_ECKPT);
+    h = fnv_words(h, host.data(), nr * row_bytes);
+    if (cudaMemcpyAsync(ctx->io, host.data(), nr * row_bytes, cudaMemcpyHostToDevice, ctx->stream) !=
+            cudaSuccess ||
+        launch_import_packed(ctx->lat, ctx->g, j0, nr, (const uint32_t*)ctx->io, ctx->hcar, ctx->col0,
+                             ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+      return bail(KPZ_ECUDA);
+  }
+  uint64_t want = 0;
+  if (fread(&want, sizeof(want), 1, in.f) != 1 || want != h || fgetc(in.f) != EOF) return bail(KPZ_ECKPT);
+  unsigned long long small[2] = {(unsigned long long)hd.t_mcs, (unsigned long long)hd.h00};
+  if (cudaMemcpyAsync(ctx->t_dev, small, sizeof(small), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+      cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+    return bail(KPZ_ECUDA);
+  ctx->t_host = hd.t_mcs;
+  *out = ctx;
   return KPZ_OK;
 }
 
