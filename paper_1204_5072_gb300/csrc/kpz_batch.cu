@@ -22,7 +22,8 @@
 #include <vector>
 
 #include "kpz.h"
-#include "kpz_tile.cuh"
+#include "kpz_run.cuh"
+#include "kpz_w2.cuh"
 
 namespace kpz {
 namespace batch {
@@ -53,7 +54,7 @@ struct Plan {
   unsigned long long* head;      // next queue index
   unsigned long long* sweep_done;
   unsigned long long* sample_done;
-  unsigned long long* acc;       // [realisation][sample index][S1, S2 lo, S2 hi]
+  unsigned long long* acc;       // [band of all realisations][sample index][D, S1, S2] (band-relative)
   uint32_t nG;                   // sample times
   int* err;                      // set to 1 when a wait ran out of time
   unsigned long long timeout_ns;
@@ -108,17 +109,15 @@ __device__ __forceinline__ int sigma_y0(const uint32_t* lat, const Geometry& g, 
   return ((b ^ bn) == ((m + g.par) & 1u)) ? 1 : -1;
 }
 
-// Exact S1, S2 (gauge h(0,0) = 0) of rows 128k .. 128k+127 of a lattice: lane
-// l takes cell row R = 32k + l, i.e. rows 4R .. 4R+3 (eq. Wdef).
-__device__ void band_sums(const SweepParams& P, uint32_t k, uint32_t lane, long long& s1,
-                          unsigned long long& s2) {
+// W^2 band k of a lattice (rows 128k .. 128k+127; lane l takes cell row
+// R = 32k + l, i.e. rows 4R .. 4R+3): the column-0 height change D over the
+// band and the sums S1 = sum h, S2 = sum h^2 of its heights relative to
+// h(0, 128k) (eq. Wdef). The host chains the bands: band k starts at the sum
+// of the D of the bands above it. tl = the lane's copy of the run table.
+__device__ void band_sums(const SweepParams& P, const uint32_t* tl, uint32_t k, uint32_t lane,
+                          long long& d, long long& s1, unsigned long long& s2) {
   const Geometry g = P.g;
   const uint32_t* lat = P.lat;
-  // h(0, 128k): column-0 slopes above the band, split over the lanes.
-  int base = 0;
-  for (uint32_t m = lane * 4u * k; m < (lane + 1u) * 4u * k; ++m) base += sigma_y0(lat, g, m);
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) base += __shfl_xor_sync(0xffffffffu, base, off);
   const uint32_t R = 32u * k + lane;
   int own[4], tot = 0;
 #pragma unroll
@@ -129,41 +128,34 @@ __device__ void band_sums(const SweepParams& P, uint32_t k, uint32_t lane, long 
     const int v = __shfl_up_sync(0xffffffffu, incl, off);
     if ((int)lane >= off) incl += v;
   }
-  long long H0 = base + incl - tot;  // h(0, 4R)
+  d = __shfl_sync(0xffffffffu, incl, 31);
+  long long H0 = incl - tot;  // h(0, 4R) - h(0, 128k)
   s1 = 0;
   s2 = 0;
 #pragma unroll 1
   for (uint32_t y4 = 0; y4 < 4; ++y4) {
     const uint32_t j = 4u * R + y4;
     long long H = H0;
-    uint32_t Pl[4];
+    uint32_t Pl[4], Pn[4];
 #pragma unroll
-    for (uint32_t x4 = 0; x4 < 4; ++x4) Pl[x4] = __ldcg(lat + g.word(0, plane(y4, x4), R));
+    for (uint32_t x4 = 0; x4 < 4; ++x4) {
+      Pl[x4] = __ldcg(lat + g.word(0, plane(y4, x4), R));
+      Pn[x4] = __ldcg(lat + g.word(1u & (g.NB - 1u), plane(y4, x4), R));
+    }
     for (uint32_t K = 0; K < g.NB; ++K) {
-      uint32_t Pn[4];
-      const uint32_t Kn = (K + 1u) & (g.NB - 1u);
+      uint32_t Pnn[4];   // two blocks ahead
+      const uint32_t K2 = (K + 2u) & (g.NB - 1u);
 #pragma unroll
-      for (uint32_t x4 = 0; x4 < 4; ++x4) Pn[x4] = __ldcg(lat + g.word(Kn, plane(y4, x4), R));
+      for (uint32_t x4 = 0; x4 < 4; ++x4) Pnn[x4] = __ldcg(lat + g.word(K2, plane(y4, x4), R));
       uint32_t S[4];  // bit c: sigma_x(128K + 4c + x4, j) = +1
-#pragma unroll
-      for (uint32_t x4 = 0; x4 < 4; ++x4) {
-        const uint32_t right = (x4 < 3) ? Pl[x4 < 3 ? x4 + 1 : 0] : ((Pl[0] >> 1) | ((Pn[0] & 1u) << 31));
-        S[x4] = ~(right ^ Pl[x4] ^ (((x4 + j + g.par) & 1u) ? ~0u : 0u));
-      }
-      int32_t h = 0, a1 = 0, a2 = 0;
-#pragma unroll 8
-      for (uint32_t c = 0; c < 32; ++c)
-#pragma unroll
-        for (uint32_t x4 = 0; x4 < 4; ++x4) {
-          a1 += h;
-          a2 += h * h;
-          h += 2 * (int32_t)((S[x4] >> c) & 1u) - 1;
-        }
+      w2::sigma_x_planes(Pl, Pn[0] & 1u, j, g.par, S);
+      int32_t h, a1, a2;
+      w2::block_sums(tl, S, h, a1, a2);
       s1 += 128 * H + a1;
       s2 += (unsigned long long)(128 * H * H + 2 * H * (long long)a1 + (long long)a2);
       H += h;
 #pragma unroll
-      for (uint32_t x4 = 0; x4 < 4; ++x4) Pl[x4] = Pn[x4];
+      for (uint32_t x4 = 0; x4 < 4; ++x4) { Pl[x4] = Pn[x4]; Pn[x4] = Pnn[x4]; }
     }
     H0 += own[y4];
   }
@@ -172,15 +164,16 @@ __device__ void band_sums(const SweepParams& P, uint32_t k, uint32_t lane, long 
 // Per-warp shared memory. 16-byte aligned size: the slab copies are 16-byte
 // cp.async writes, so every warp's slot must start on a 16-byte boundary.
 struct alignas(16) WarpSlot {
-  tile::WarpStage stage;
+  run::WarpStage<1> stage;
   SweepParams P;
 };
 static_assert(sizeof(WarpSlot) % 16 == 0, "warp slots must keep 16-byte alignment");
-static_assert(sizeof(tile::WarpStage) % 16 == 0, "slab rows must keep 16-byte alignment");
 
 __global__ void __launch_bounds__(256, 2) batch_kernel(const __grid_constant__ Plan Q) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSlot& ws = reinterpret_cast<WarpSlot*>(smem_raw)[threadIdx.x >> 5];
+  __shared__ uint32_t tab[w2::kRunTableWords];   // W^2 run table (kpz_w2.cuh)
+  w2::fill_run_table(tab);
   const uint32_t lane = threadIdx.x & 31u;
   for (;;) {
     unsigned long long idx = 0;
@@ -232,25 +225,28 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(const __grid_constant__ P
     __syncwarp();
 
     if (is_sample) {
-      long long s1;
+      long long d, s1;
       unsigned long long s2;
-      band_sums(ws.P, (uint32_t)k, lane, s1, s2);
+      band_sums(ws.P, tab + lane, (uint32_t)k, lane, d, s1, s2);
 #pragma unroll
-      for (int d = 16; d > 0; d >>= 1) {
-        s1 += __shfl_xor_sync(0xffffffffu, s1, d);
-        s2 += __shfl_xor_sync(0xffffffffu, s2, d);
+      for (int off = 16; off > 0; off >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, off);
       }
       if (lane == 0) {
-        unsigned long long* a = Q.acc + ((size_t)i * Q.nG + (sg.nsamp - 1u)) * 3u;
-        atomicAdd(&a[0], (unsigned long long)s1);
-        const unsigned long long old = atomicAdd(&a[1], s2);
-        if (old + s2 < old) atomicAdd(&a[2], 1ull);
+        unsigned long long* a = Q.acc + ((size_t)(Q.PS[i] + k) * Q.nG + (sg.nsamp - 1u)) * 3u;
+        a[0] = (unsigned long long)d;
+        a[1] = (unsigned long long)s1;
+        a[2] = s2;
       }
     } else {
       const uint32_t ty = (uint32_t)(k / ws.P.runs_x);
       const uint32_t tx0 = (uint32_t)(k - (unsigned long long)ty * ws.P.runs_x) * ws.P.run;
-      if (general) tile::run_tiles<true>(ws.P, g, ty, tx0, ws.stage, lane);
-      else         tile::run_tiles<false>(ws.P, g, ty, tx0, ws.stage, lane);
+      // Device layer: this sweep's random tile origin (Sec. 3).
+      const uint4 o = philox(kTagOrigin << 28, 0u, g, ws.P.sample, ws.P.k0, ws.P.k1);
+      const uint32_t L = ws.P.g.L, ox = o.x & (L - 1u), oy = o.y & (L - 1u);
+      if (general) run::sweep_run<true, 1, false, true>(ws.P, ws.stage, nullptr, lane, g, ox, oy, ty, tx0, ws.P.run);
+      else         run::sweep_run<false, 1, false, true>(ws.P, ws.stage, nullptr, lane, g, ox, oy, ty, tx0, ws.P.run);
     }
     __threadfence();
     __syncwarp();
@@ -282,6 +278,7 @@ struct kpz_batch {
   void* pool = nullptr;
   size_t pool_bytes = 0;
   size_t lat_bytes = 0;              // lattices at the start of the pool
+  size_t bands = 0;                  // W^2 bands of all realisations (sum of L/128)
   Plan plan{};
   std::vector<Real> real;            // host copy of the sorted realisation table
   cudaGraphExec_t exec = nullptr;
@@ -387,7 +384,11 @@ kpz_status fail_free(kpz_batch* b, kpz_status st) {
 kpz_status allocate(kpz_batch* b) {
   const uint32_t n = (uint32_t)b->spec.size();
   size_t lat = 0;
-  for (const auto& s : b->spec) lat += up256((size_t)s.L * s.L / 8);
+  b->bands = 0;
+  for (const auto& s : b->spec) {
+    lat += up256((size_t)s.L * s.L / 8);
+    b->bands += s.L / 128u;
+  }
   b->lat_bytes = lat;
   // worst-case table sizes (run length 1 gives the most items, not more segments)
   const size_t nseg_max = 2 * b->times.size() + 4;
@@ -396,7 +397,7 @@ kpz_status allocate(kpz_batch* b) {
   bytes += up256(sizeof(Real) * n) + up256(sizeof(Segment) * nseg_max);
   bytes += 2 * up256(8 * (n + 1));                 // PW, PS
   bytes += 2 * up256(8 * n) + up256(8 * n);        // sweep_done, sample_done, h00
-  bytes += up256(24 * n * nG) + 256 + 256;         // acc, head, err
+  bytes += up256(24 * b->bands * nG) + 256 + 256;  // band partials, head, err
   if (cudaMalloc(&b->pool, bytes) != cudaSuccess) { cudaGetLastError(); return KPZ_ENOMEM; }
   b->pool_bytes = bytes;
   return KPZ_OK;
@@ -420,7 +421,7 @@ PoolMap map_pool(const kpz_batch* b) {
   m.sweep_done = (unsigned long long*)p; p += up256(8 * n);
   m.sample_done = (unsigned long long*)p; p += up256(8 * n);
   m.h00 = (unsigned long long*)p; p += up256(8 * n);
-  m.acc = (unsigned long long*)p; p += up256(24 * n * nG);
+  m.acc = (unsigned long long*)p; p += up256(24 * b->bands * nG);
   m.head = (unsigned long long*)p; p += 256;
   m.err = (int*)p;
   return m;
@@ -639,18 +640,32 @@ kpz_status kpz_batch_sums(const kpz_batch* b, int64_t* S1, uint64_t* S2_lo, uint
   if (!b->ran) return KPZ_ESTATE;
   const size_t n = b->spec.size(), nG = b->times.size();
   PoolMap m = map_pool(b);
-  std::vector<unsigned long long> acc(3 * n * nG), h(n);
-  if (cudaMemcpy(acc.data(), m.acc, 24 * n * nG, cudaMemcpyDeviceToHost) != cudaSuccess ||
+  std::vector<unsigned long long> acc(3 * b->bands * nG), h(n);
+  if (cudaMemcpy(acc.data(), m.acc, 24 * b->bands * nG, cudaMemcpyDeviceToHost) != cudaSuccess ||
       cudaMemcpy(h.data(), m.h00, 8 * n, cudaMemcpyDeviceToHost) != cudaSuccess)
     return KPZ_ECUDA;
+  // Chain the bands of each sample (eq. Wdef): band k starts at height H_k =
+  // sum of the column-0 changes D of the bands above it; a band of n_b sites
+  // with relative sums (s1, s2) adds n_b H + s1 and n_b H^2 + 2 H s1 + s2.
+  size_t band0 = 0;
   for (size_t i = 0; i < n; ++i) {
     const size_t c = b->order[i];
+    const uint32_t L = b->spec[c].L, nb = L / 128u;
+    const __int128 nsite = (__int128)128 * L;
     for (size_t k = 0; k < nG; ++k) {
-      const unsigned long long* a = &acc[3 * (i * nG + k)];
-      S1[c * nG + k] = (int64_t)a[0];
-      S2_lo[c * nG + k] = a[1];
-      S2_hi[c * nG + k] = a[2];
+      __int128 H = 0, s1 = 0, s2 = 0;
+      for (uint32_t q = 0; q < nb; ++q) {
+        const unsigned long long* a = &acc[3 * ((band0 + q) * nG + k)];
+        const __int128 bs1 = (long long)a[1], bs2 = (__int128)a[2];
+        s1 += nsite * H + bs1;
+        s2 += nsite * H * H + 2 * H * bs1 + bs2;
+        H += (long long)a[0];
+      }
+      S1[c * nG + k] = (int64_t)s1;
+      S2_lo[c * nG + k] = (uint64_t)((unsigned __int128)s2);
+      S2_hi[c * nG + k] = (uint64_t)((unsigned __int128)s2 >> 64);
     }
+    band0 += nb;
     if (h00) h00[c] = (int64_t)h[i];
   }
   return KPZ_OK;

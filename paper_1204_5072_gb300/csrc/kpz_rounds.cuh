@@ -38,6 +38,7 @@ struct TileCtx {
   bool track;             // this tile contains site (0,0)
   uint32_t xo, yo, co, cyo;  // site (0,0): column, row in the cell, cell, cell row
   const uint4* rk;        // round keys in shared memory (kSK)
+  uint32_t pm;            // all ones when the tile's site (0,0) is odd (run-time parity)
 };
 
 template <bool kSK>
@@ -79,13 +80,17 @@ __device__ __forceinline__ void acceptance(const SweepParams& P, const TileCtx& 
   AQ = (P.Tq >> 16) ? ~0u : ltq;
 }
 
-// One single-hit round with active quadrant (QX, QY); kPar = parity of the
-// tile's site (0,0); Xi[r], Yi[r]: position bits of cell row r.
-template <int QX, int QY, bool kGeneral, int kPar, bool kTrack, int CR, bool kSK>
-__device__ __forceinline__ void quad_round(uint32_t (&T)[CR][4][4], const uint32_t (&Xi)[CR],
+// Selected local minima (fmin) and maxima (fmax) of one single-hit round with
+// active quadrant (QX, QY), from the state before the round, for every cell
+// row; fmax only with kGeneral. kPar = parity of the tile's site (0,0), or 2:
+// taken at run time from tc.pm (all ones when odd). Xi[r], Yi[r]: position
+// bits of cell row r. Selected sites are never neighbours of each other, so
+// masks taken before any flip equal masks taken site by site.
+template <int QX, int QY, bool kGeneral, int kPar, int CR>
+__device__ __forceinline__ void quad_masks(const uint32_t (&T)[CR][4][4], const uint32_t (&Xi)[CR],
                                            const uint32_t (&Yi)[CR], const uint32_t (&hx)[CR][4],
-                                           const uint32_t (&hy)[4], const SweepParams& P,
-                                           const TileCtx& tc, uint32_t lane, uint32_t r, int& dh) {
+                                           const uint32_t (&hy)[4], const TileCtx& tc,
+                                           uint32_t (&fmin)[CR][2][2], uint32_t (&fmax)[CR][2][2]) {
   constexpr int x0 = 2 * QX, y0 = 2 * QY;
   // The one y-neighbour per column that lies in another lane.
   uint32_t ysh[2];
@@ -115,7 +120,6 @@ __device__ __forceinline__ void quad_round(uint32_t (&T)[CR][4][4], const uint32
       if (QY == 0) yn[d] = (row > 0) ? T[row > 0 ? row - 1 : 0][3][x0 + d] : ysh[d];
       else         yn[d] = (row < CR - 1) ? T[row < CR - 1 ? row + 1 : 0][0][x0 + d] : ysh[d];
     }
-    uint32_t fmin[2][2], fmax[2][2];
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
@@ -126,45 +130,87 @@ __device__ __forceinline__ void quad_round(uint32_t (&T)[CR][4][4], const uint32
         const uint32_t nR = (xp < 3) ? T[row][yp][xp < 3 ? xp + 1 : 3] : xn[dy];
         const uint32_t nU = (yp > 0) ? T[row][yp > 0 ? yp - 1 : 0][xp] : yn[dx];
         const uint32_t nD = (yp < 3) ? T[row][yp < 3 ? yp + 1 : 3][xp] : yn[dx];
-        const uint32_t v = ((kPar + xp + yp) & 1) ? ~s : s;   // bit of a higher neighbour
+        uint32_t v;   // bit of a higher neighbour
+        if (kPar == 2) v = s ^ (((xp + yp) & 1) ? ~tc.pm : tc.pm);
+        else           v = ((kPar + xp + yp) & 1) ? ~s : s;
         const uint32_t hL = ~(nL ^ v), hR = ~(nR ^ v), hU = ~(nU ^ v), hD = ~(nD ^ v);
-        fmin[dy][dx] = sel[dy][dx] & hL & hR & hU & hD;                       // local minimum
-        fmax[dy][dx] = kGeneral ? (sel[dy][dx] & ~hL & ~hR & ~hU & ~hD) : 0u;  // local maximum
+        fmin[row][dy][dx] = sel[dy][dx] & hL & hR & hU & hD;                       // local minimum
+        fmax[row][dy][dx] = kGeneral ? (sel[dy][dx] & ~hL & ~hR & ~hU & ~hD) : 0u;  // local maximum
       }
-    if (kGeneral) {
-      uint32_t AP, AQ;
-      acceptance<kSK>(P, tc, CR * lane + row, r, fmin[0][0] | fmin[0][1] | fmin[1][0] | fmin[1][1],
-                 fmax[0][0] | fmax[0][1] | fmax[1][0] | fmax[1][1], AP, AQ);
+  }
+}
+
+// Apply the accepted moves of a round with active quadrant (QX, QY): count
+// those of site (0,0) when the tile holds it, then toggle the bits.
+template <int QX, int QY, bool kTrack, int CR>
+__device__ __forceinline__ void quad_flips(uint32_t (&T)[CR][4][4], const uint32_t (&fmin)[CR][2][2],
+                                           const uint32_t (&fmax)[CR][2][2], const TileCtx& tc,
+                                           uint32_t lane, int& dh) {
+  constexpr int x0 = 2 * QX, y0 = 2 * QY;
 #pragma unroll
-      for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-        for (int dx = 0; dx < 2; ++dx) { fmin[dy][dx] &= AP; fmax[dy][dx] &= AQ; }
-    }
+  for (int row = 0; row < CR; ++row) {
     if (kTrack && CR * lane + row == tc.cyo) {
 #pragma unroll
       for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
         for (int dx = 0; dx < 2; ++dx)
           if ((uint32_t)(x0 + dx) == tc.xo && (uint32_t)(y0 + dy) == tc.yo)
-            dh += 2 * (int)((fmin[dy][dx] >> tc.co) & 1u) - 2 * (int)((fmax[dy][dx] >> tc.co) & 1u);
+            dh += 2 * (int)((fmin[row][dy][dx] >> tc.co) & 1u) - 2 * (int)((fmax[row][dy][dx] >> tc.co) & 1u);
     }
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-      for (int dx = 0; dx < 2; ++dx) T[row][y0 + dy][x0 + dx] ^= fmin[dy][dx] | fmax[dy][dx];
+      for (int dx = 0; dx < 2; ++dx) T[row][y0 + dy][x0 + dx] ^= fmin[row][dy][dx] | fmax[row][dy][dx];
   }
 }
 
+// One single-hit round (Sec. 3.1): the quadrant set k of round r is uniform
+// over the warp, so the round dispatches once on it. The p = 1, q = 0 path
+// takes masks and flips in one branch; the general path takes the masks in
+// one branch, decides acceptance for all quadrants with the same code (one
+// copy of the acceptance draws), then flips in a second branch.
 template <bool kGeneral, int kPar, bool kTrack, int CR, bool kSK>
 __device__ __forceinline__ void one_round(uint32_t (&T)[CR][4][4], const uint32_t (&Xi)[CR],
                                           const uint32_t (&Yi)[CR], const uint32_t (&hx)[CR][4],
                                           const uint32_t (&hy)[4], const SweepParams& P,
                                           const TileCtx& tc, uint32_t lane, uint32_t r, int& dh) {
-  switch ((tc.setw >> (2u * r)) & 3u) {
-    case 0: quad_round<0, 0, kGeneral, kPar, kTrack, CR, kSK>(T, Xi, Yi, hx, hy, P, tc, lane, r, dh); break;
-    case 1: quad_round<1, 0, kGeneral, kPar, kTrack, CR, kSK>(T, Xi, Yi, hx, hy, P, tc, lane, r, dh); break;
-    case 2: quad_round<0, 1, kGeneral, kPar, kTrack, CR, kSK>(T, Xi, Yi, hx, hy, P, tc, lane, r, dh); break;
-    default: quad_round<1, 1, kGeneral, kPar, kTrack, CR, kSK>(T, Xi, Yi, hx, hy, P, tc, lane, r, dh); break;
+  const uint32_t k = (tc.setw >> (2u * r)) & 3u;
+  uint32_t fmin[CR][2][2], fmax[CR][2][2];
+  if (!kGeneral) {
+    switch (k) {
+      case 0: quad_masks<0, 0, false, kPar, CR>(T, Xi, Yi, hx, hy, tc, fmin, fmax);
+              quad_flips<0, 0, kTrack, CR>(T, fmin, fmax, tc, lane, dh); break;
+      case 1: quad_masks<1, 0, false, kPar, CR>(T, Xi, Yi, hx, hy, tc, fmin, fmax);
+              quad_flips<1, 0, kTrack, CR>(T, fmin, fmax, tc, lane, dh); break;
+      case 2: quad_masks<0, 1, false, kPar, CR>(T, Xi, Yi, hx, hy, tc, fmin, fmax);
+              quad_flips<0, 1, kTrack, CR>(T, fmin, fmax, tc, lane, dh); break;
+      default: quad_masks<1, 1, false, kPar, CR>(T, Xi, Yi, hx, hy, tc, fmin, fmax);
+               quad_flips<1, 1, kTrack, CR>(T, fmin, fmax, tc, lane, dh); break;
+    }
+    return;
+  }
+  switch (k) {
+    case 0: quad_masks<0, 0, true, kPar, CR>(T, Xi, Yi, hx, hy, tc, fmin, fmax); break;
+    case 1: quad_masks<1, 0, true, kPar, CR>(T, Xi, Yi, hx, hy, tc, fmin, fmax); break;
+    case 2: quad_masks<0, 1, true, kPar, CR>(T, Xi, Yi, hx, hy, tc, fmin, fmax); break;
+    default: quad_masks<1, 1, true, kPar, CR>(T, Xi, Yi, hx, hy, tc, fmin, fmax); break;
+  }
+#pragma unroll
+  for (int row = 0; row < CR; ++row) {
+    uint32_t AP, AQ;
+    acceptance<kSK>(P, tc, CR * lane + row, r,
+                    fmin[row][0][0] | fmin[row][0][1] | fmin[row][1][0] | fmin[row][1][1],
+                    fmax[row][0][0] | fmax[row][0][1] | fmax[row][1][0] | fmax[row][1][1], AP, AQ);
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx) { fmin[row][dy][dx] &= AP; fmax[row][dy][dx] &= AQ; }
+  }
+  switch (k) {
+    case 0: quad_flips<0, 0, kTrack, CR>(T, fmin, fmax, tc, lane, dh); break;
+    case 1: quad_flips<1, 0, kTrack, CR>(T, fmin, fmax, tc, lane, dh); break;
+    case 2: quad_flips<0, 1, kTrack, CR>(T, fmin, fmax, tc, lane, dh); break;
+    default: quad_flips<1, 1, kTrack, CR>(T, fmin, fmax, tc, lane, dh); break;
   }
 }
 
@@ -185,16 +231,6 @@ __device__ __forceinline__ void tile_rounds(uint32_t (&T)[CR][4][4], const uint3
     one_round<kGeneral, kPar, kTrack, CR, kSK>(T, X0, Y0, hx, hy, P, tc, lane, 2u * rp, dh);
     one_round<kGeneral, kPar, kTrack, CR, kSK>(T, X1, Y1, hx, hy, P, tc, lane, 2u * rp + 1u, dh);
   }
-}
-
-// One cell row per lane (128 x 128 tiles), registers as T[y'][x'], hx[y'].
-template <bool kGeneral, int kPar, bool kTrack>
-__device__ __forceinline__ void tile_rounds(uint32_t (&T)[4][4], const uint32_t (&hx)[4],
-                                            const uint32_t (&hy)[4], const SweepParams& P,
-                                            const TileCtx& tc, uint32_t lane, int& dh) {
-  tile_rounds<kGeneral, kPar, kTrack, 1, false>(reinterpret_cast<uint32_t(&)[1][4][4]>(T),
-                                         reinterpret_cast<const uint32_t(&)[1][4]>(hx), hy, P, tc,
-                                         lane, dh);
 }
 
 }  // namespace rounds
