@@ -120,10 +120,8 @@ void orc_init_flat(uint32_t L, uint8_t* sx, uint8_t* sy) {
  * pattern (+1,-1 ; +1,-1) a local maximum. A flip negates all four slopes,
  * which moves h(i,j) by +2 (minimum, if acc_min) or -2 (maximum, if acc_max).
  * Returns the height change of the site. */
-int orc_attempt(uint32_t L, uint8_t* sx, uint8_t* sy, uint32_t i, uint32_t j,
-                int acc_min, int acc_max) {
-    uint32_t im = (i + L - 1) & (L - 1), jm = (j + L - 1) & (L - 1);
-    size_t here = (size_t)j * L + i, left = (size_t)j * L + im, below = (size_t)jm * L + i;
+static int attempt_at(uint8_t* sx, uint8_t* sy, size_t here, size_t left, size_t below,
+                      int acc_min, int acc_max) {
     int a = sx[left], b = sx[here], c = sy[below], d = sy[here];
     int is_min = (a == 0 && b == 1 && c == 0 && d == 1);
     int is_max = (a == 1 && b == 0 && c == 1 && d == 0);
@@ -132,6 +130,13 @@ int orc_attempt(uint32_t L, uint8_t* sx, uint8_t* sy, uint32_t i, uint32_t j,
         return is_min ? 2 : -2;
     }
     return 0;
+}
+
+int orc_attempt(uint32_t L, uint8_t* sx, uint8_t* sy, uint32_t i, uint32_t j,
+                int acc_min, int acc_max) {
+    uint32_t im = (i + L - 1) & (L - 1), jm = (j + L - 1) & (L - 1);
+    size_t here = (size_t)j * L + i, left = (size_t)j * L + im, below = (size_t)jm * L + i;
+    return attempt_at(sx, sy, here, left, below, acc_min, acc_max);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -200,6 +205,58 @@ static void shuffle(uint32_t* a, uint32_t n, uint64_t state) {
     }
 }
 
+/* The 16 single-hit rounds of tile T of sweep s (work-group layer, Sec. 3.1).
+ * win == NULL: (sx, sy) is the L x L lattice. win != NULL: (sx, sy) hold only
+ * this tile's Bx x By window (row-major, stride Bx, local (u, v) = global
+ * ((x0 + u) mod L, (y0 + v) mod L)); an attempt at live (u, v), u, v >= 1,
+ * reads and writes sigma_x(u-1, v), sigma_x(u, v), sigma_y(u, v-1),
+ * sigma_y(u, v), all inside the window, so a tile evolves from its window
+ * alone; *win receives the height change of global site (0, 0) if the tile
+ * holds it. cell_order is scratch for Bx*By/16 entries. */
+static void tile_rounds(const orc_params* P, uint32_t s, uint32_t T, uint32_t ox, uint32_t oy,
+                        uint32_t rounds, uint64_t order, uint32_t* cell_order, memo* mpos,
+                        memo* macc, uint8_t* sx, uint8_t* sy, int64_t* win, int64_t* h00) {
+    uint32_t L = P->L, Bx = P->Bx, By = P->By;
+    uint32_t ntx = L / Bx;
+    uint32_t ncx = Bx / 4, ncy = By / 4, ncells = ncx * ncy;
+    uint32_t tx = T % ntx, ty = T / ntx;
+    uint32_t x0 = ox + tx * Bx, y0 = oy + ty * By;
+    uint32_t setw[4];
+    philox_at((uint32_t)TAG_SET << 28, T, s, P->sample, P->seed, setw);
+
+    /* Work-group layer: 16 single-hit rounds; each picks one of the four
+     * quadrant sets at random (possibly the same as before) and gives every
+     * cell one attempt inside its active quadrant. */
+    for (uint32_t r = 0; r < rounds; ++r) {
+        uint32_t k = (setw[0] >> (2 * r)) & 3u;
+        uint32_t qx = k & 1u, qy = k >> 1;
+        shuffle(cell_order, ncells, order >= 2 ? order * 0x9E3779B97F4A7C15ull + T + 1 : 0);
+        if (order == 1)
+            for (uint32_t c = 0; c < ncells; ++c) cell_order[c] = ncells - 1 - c;
+        for (uint32_t c = 0; c < ncells; ++c) {
+            uint32_t cell = cell_order[c];
+            uint32_t cx = cell % ncx, cy = cell / ncx;
+            uint32_t xi, yi;
+            position_bits(P, mpos, T, s, cx, cy, r, &xi, &yi);
+            uint32_t u = 4 * cx + 2 * qx + xi;
+            uint32_t v = 4 * cy + 2 * qy + yi;
+            if (u == 0 || v == 0) continue;          /* dead border of the tile */
+            uint32_t i = (x0 + u) & (L - 1), j = (y0 + v) & (L - 1);
+            uint32_t U = acceptance_number(P, macc, T, s, cx, cy, r);
+            int dh;
+            if (win)
+                dh = attempt_at(sx, sy, (size_t)v * Bx + u, (size_t)v * Bx + u - 1,
+                                (size_t)(v - 1) * Bx + u, U < P->Tp, U < P->Tq);
+            else
+                dh = orc_attempt(L, sx, sy, i, j, U < P->Tp, U < P->Tq);
+            if (dh != 0 && i == 0 && j == 0) {
+                if (h00) *h00 += dh;
+                if (win) *win += dh;
+            }
+        }
+    }
+}
+
 /* ------------------------------------------------------------------------- */
 /* One sweep of the decomposed dynamics (Sec. 3 and 3.1).                      */
 /* order: 0 = tiles and cells in natural order, 1 = both reversed, >= 2 = both */
@@ -233,37 +290,46 @@ int orc_sweep(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32_t Tq,
     memo mpos = {0}, macc[4] = {{0}};
     for (uint32_t n = 0; n < ntiles; ++n) {
         uint32_t T = tile_order[n];
-        uint32_t tx = T % ntx, ty = T / ntx;
-        uint32_t x0 = ox + tx * Bx, y0 = oy + ty * By;
-        uint32_t setw[4];
-        philox_at((uint32_t)TAG_SET << 28, T, s, sample, seed, setw);
-
-        /* Work-group layer: 16 single-hit rounds; each picks one of the four
-         * quadrant sets at random (possibly the same as before) and gives every
-         * cell one attempt inside its active quadrant. */
-        for (uint32_t r = 0; r < rounds; ++r) {
-            uint32_t k = (setw[0] >> (2 * r)) & 3u;
-            uint32_t qx = k & 1u, qy = k >> 1;
-            shuffle(cell_order, ncells, order >= 2 ? order * 0x9E3779B97F4A7C15ull + T + 1 : 0);
-            if (order == 1)
-                for (uint32_t c = 0; c < ncells; ++c) cell_order[c] = ncells - 1 - c;
-            for (uint32_t c = 0; c < ncells; ++c) {
-                uint32_t cell = cell_order[c];
-                uint32_t cx = cell % ncx, cy = cell / ncx;
-                uint32_t xi, yi;
-                position_bits(&P, &mpos, T, s, cx, cy, r, &xi, &yi);
-                uint32_t u = 4 * cx + 2 * qx + xi;
-                uint32_t v = 4 * cy + 2 * qy + yi;
-                if (u == 0 || v == 0) continue;          /* dead border of the tile */
-                uint32_t i = (x0 + u) & (L - 1), j = (y0 + v) & (L - 1);
-                uint32_t U = acceptance_number(&P, macc, T, s, cx, cy, r);
-                int dh = orc_attempt(L, sx, sy, i, j, U < Tp, U < Tq);
-                if (dh != 0 && i == 0 && j == 0 && h00) *h00 += dh;
-            }
-        }
+        tile_rounds(&P, s, T, ox, oy, rounds, order, cell_order, &mpos, macc, sx, sy, NULL, h00);
     }
     free(tile_order);
     free(cell_order);
+    return 0;
+}
+
+/* Tile T of sweep s started from the flat configuration (Sec. 2.1), computed
+ * on its own Bx x By window: (sx_win, sy_win) receive the window's slopes after
+ * the sweep (row-major, stride Bx, local (u, v) = global ((x0+u) mod L,
+ * (y0+v) mod L) with (x0, y0) the tile's anchor), *anchor_x / *anchor_y the
+ * anchor, *dh00 the height change of site (0, 0) (0 unless the tile holds it).
+ * Exact for a lattice that is flat when sweep s starts (tiles of one sweep do
+ * not interact). Returns 0, or -1 on bad input. */
+int orc_flat_tile_sweep(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32_t Tq,
+                        uint64_t seed, uint32_t sample, uint32_t s, uint32_t T,
+                        uint8_t* sx_win, uint8_t* sy_win, uint32_t* anchor_x, uint32_t* anchor_y,
+                        int64_t* dh00) {
+    if (L < 4 || (L & (L - 1)) || Bx < 4 || By < 4 || (Bx & (Bx - 1)) || (By & (By - 1)) ||
+        Bx > L || By > L || Tp > 65536u || Tq > 65536u || T >= (L / Bx) * (L / By))
+        return -1;
+    orc_params P = {L, Bx, By, Tp, Tq, sample, seed};
+    uint32_t w[4];
+    philox_at((uint32_t)TAG_ORIGIN << 28, 0, s, sample, seed, w);
+    uint32_t ox = w[0] & (L - 1), oy = w[1] & (L - 1);
+    uint32_t ntx = L / Bx, tx = T % ntx, ty = T / ntx;
+    uint32_t x0 = (ox + tx * Bx) & (L - 1), y0 = (oy + ty * By) & (L - 1);
+    for (uint32_t v = 0; v < By; ++v)
+        for (uint32_t u = 0; u < Bx; ++u) {
+            uint8_t up = (((x0 + u) + (y0 + v)) & 1u) == 0u;   /* flat start */
+            sx_win[(size_t)v * Bx + u] = up;
+            sy_win[(size_t)v * Bx + u] = up;
+        }
+    uint32_t* cell_order = (uint32_t*)malloc(sizeof(uint32_t) * (Bx / 4) * (By / 4));
+    if (!cell_order) return -1;
+    memo mpos = {0}, macc[4] = {{0}};
+    int64_t d = 0;
+    tile_rounds(&P, s, T, ox, oy, 16, 0, cell_order, &mpos, macc, sx_win, sy_win, &d, NULL);
+    free(cell_order);
+    *anchor_x = x0; *anchor_y = y0; *dh00 = d;
     return 0;
 }
 

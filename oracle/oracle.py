@@ -68,6 +68,11 @@ def lib():
             L.orc_w2.restype = c.c_double
             L.orc_pack.argtypes = [c.c_uint32, u8p, u8p, u32p]
             L.orc_unpack.argtypes = [c.c_uint32, u32p, u8p, u8p]
+            L.orc_flat_tile_sweep.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32,
+                                              c.c_uint64, c.c_uint32, c.c_uint32, c.c_uint32, u8p, u8p,
+                                              c.POINTER(c.c_uint32), c.POINTER(c.c_uint32),
+                                              c.POINTER(c.c_int64)]
+            L.orc_flat_tile_sweep.restype = c.c_int
             _lib = L
     return _lib
 
@@ -83,6 +88,21 @@ def philox(ctr, key) -> np.ndarray:
 def threshold(p: float) -> int:
     """Acceptance threshold out of 2^16 used for probability ``p``."""
     return int(lib().orc_threshold(float(p)))
+
+
+def flat_tile_sweep(L, Bx, By, p, q, seed, sample, s, T):
+    """Tile T of sweep s from the flat start, computed on its own window (the
+    tiles of one sweep do not interact): returns (sx, sy) of shape (By, Bx)
+    indexed [v, u] = global site ((x0+u) mod L, (y0+v) mod L), the anchor
+    (x0, y0), and the height change of site (0, 0)."""
+    sx = np.zeros(By * Bx, np.uint8)
+    sy = np.zeros(By * Bx, np.uint8)
+    ax, ay, d = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_int64()
+    rc = lib().orc_flat_tile_sweep(L, Bx, By, threshold(p), threshold(q), seed, sample, s, T, sx, sy,
+                                   ctypes.byref(ax), ctypes.byref(ay), ctypes.byref(d))
+    if rc:
+        raise ValueError("bad arguments")
+    return sx.reshape(By, Bx), sy.reshape(By, Bx), (ax.value, ay.value), d.value
 
 
 class State:

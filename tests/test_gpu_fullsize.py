@@ -1,10 +1,13 @@
-"""Properties of the CUDA engine at the benchmark's full size (L = 2^16) and at
-the largest accepted size, where the oracle cannot follow every site:
-a valid surface (every row of sigma_x and every column of sigma_y sums to
-zero, Sec. 2.1) and the exact width computed a second, independent way."""
+"""The CUDA engine at the benchmark's full size (L = 2^16) and at the largest
+accepted size, where the oracle cannot follow every site: sampled tiles of
+the first sweep against the oracle (tiles of one sweep do not interact, so
+the oracle computes each from the flat start on its own window), a valid
+surface (every row of sigma_x and every column of sigma_y sums to zero,
+Sec. 2.1) and the exact width computed a second, independent way."""
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from tests.gpu_util import engine
 
 pytestmark = pytest.mark.gpu
@@ -82,3 +85,41 @@ def test_largest_lattice(eng):
     words = lat.slopes()
     w = words.reshape(L, L // 16)
     assert np.all(_popcount(w & np.uint32(0x55555555)).sum(axis=1, dtype=np.int64) == L // 2)
+
+
+def _window(words, L, x0, y0, Bx, By):
+    """sigma_x, sigma_y bits of the window [v, u] = site ((x0+u) mod L, (y0+v) mod L)
+    from the packed exchange format (word j*L/16 + i/16, bits 2(i%16), 2(i%16)+1)."""
+    w = words.reshape(L, L // 16)
+    rows = (y0 + np.arange(By)) % L
+    cols = (x0 + np.arange(Bx)) % L
+    sub = w[np.ix_(rows, cols // 16)]
+    sh = (2 * (cols % 16)).astype(np.uint32)
+    return ((sub >> sh) & 1).astype(np.uint8), ((sub >> (sh + 1)) & 1).astype(np.uint8)
+
+
+@pytest.mark.parametrize("p,q,ty", [(1.0, 0.0, 128), (0.95, 0.05, 128), (1.0, 0.0, 256)])
+def test_L65536_first_sweep_sampled_tiles_match_oracle(eng, p, q, ty):
+    """One sweep at L = 2^16 from the flat start in the benchmark's launch
+    configuration (default run length and warps per CTA); sampled tiles and the
+    height of site (0,0) bit-exact against the oracle's window computation."""
+    L, Bx, By, seed, sample = 65536, 128, ty, 1, 0
+    lat = eng.Lattice(L, p, q, seed=seed, sample=sample, tile_y=ty)
+    lat.run(1)
+    words = lat.slopes()
+    r = lat.roughness()
+    lat.close()
+    ntx, nty = L // Bx, L // By
+    o = O.philox([0, 0, 0, sample], [seed & 0xFFFFFFFF, seed >> 32])
+    ox, oy = int(o[0]) & (L - 1), int(o[1]) & (L - 1)
+    t00 = (((L - oy) % L) // By) * ntx + ((L - ox) % L) // Bx      # tile holding site (0,0)
+    rng = np.random.default_rng(7)
+    tiles = {0, ntx - 1, ntx * nty - 1, ntx * (nty - 1), t00} | set(rng.integers(0, ntx * nty, 16).tolist())
+    dh00 = 0
+    for T in sorted(tiles):
+        sx, sy, (x0, y0), d = O.flat_tile_sweep(L, Bx, By, p, q, seed, sample, 0, T)
+        gx, gy = _window(words, L, x0, y0, Bx, By)
+        assert np.array_equal(gx, sx) and np.array_equal(gy, sy), (p, q, ty, T)
+        if T == t00:
+            dh00 = d
+    assert r["h00"] == dh00 and r["t"] == 1

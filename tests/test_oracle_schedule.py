@@ -165,3 +165,26 @@ def test_one_round_touches_one_quadrant_per_tile(L, Bx, By):
         # every site is raised at most once in a round and at most one per cell
         cell = ((v // 4) * (L // 4) + (u // 4))
         assert len(np.unique(cell[moved])) == int(moved.sum())
+
+
+@pytest.mark.parametrize("L,Bx,By,p,q,seed,sample,s", [
+    (64, 16, 16, 1.0, 0.0, 3, 0, 0), (128, 32, 64, 0.7, 0.2, 5, 2, 4), (256, 128, 128, 0.95, 0.05, 1, 0, 0),
+    (256, 128, 256, 0.6, 0.4, 9, 1, 7)])
+def test_flat_tile_windows_assemble_the_full_sweep(L, Bx, By, p, q, seed, sample, s):
+    """Tiles of one sweep do not interact (dead border, Sec. 3): computing every
+    tile of a sweep from the flat start on its own window and placing the
+    windows at their anchors gives the full sweep, slopes and h(0,0)."""
+    st = O.State.flat(L)
+    st.sweep(Bx, By, p, q, seed, sample, s=s)
+    sx = np.zeros((L, L), np.uint8)
+    sy = np.zeros((L, L), np.uint8)
+    dh = 0
+    for T in range((L // Bx) * (L // By)):
+        wx, wy, (x0, y0), d = O.flat_tile_sweep(L, Bx, By, p, q, seed, sample, s, T)
+        rows = (y0 + np.arange(By)) % L
+        cols = (x0 + np.arange(Bx)) % L
+        sx[np.ix_(rows, cols)] = wx
+        sy[np.ix_(rows, cols)] = wy
+        dh += d
+    assert np.array_equal(sx, st.sx.reshape(L, L)) and np.array_equal(sy, st.sy.reshape(L, L))
+    assert dh == st.h00
