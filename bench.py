@@ -253,7 +253,7 @@ def batch_bench(eng, cap, seed=1):
                                           "speedup": per_real / batched},
             "workload": f"512 realisations, L=2^(8..13) log-uniform, p~U[0.5,1], q=1-p, "
                         f"T=min(4 L^1.6, {cap}) MCS, W^2 at the common log-spaced times (seed {seed})",
-            "tuning": {k: info[k] for k in ("run", "warps_per_cta", "ctas_per_sm", "grid", "graph")},
+            "tuning": {k: info[k] for k in ("run", "warps_per_cta", "ctas_per_sm", "grid", "graph", "tile_y")},
             "autotune_s": create_s}
 
 

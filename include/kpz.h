@@ -186,8 +186,9 @@ typedef struct {
     uint32_t n_samples;    /* log-spaced W^2 times up to the longest run (0 = 64);
                               every realisation is also sampled at its own end    */
     int autotune;          /* != 0: time a short probe of the ensemble for every
-                              (tiles per run, warps per block) and keep the fastest;
-                              the choice never changes the results                */
+                              (tiles per run, warps per block) and keep the fastest
+                              (that choice never changes the results); with
+                              tile_y = 0 also choose the tile height              */
     uint32_t run;          /* tiles per run when not tuning (power of two, 0 = 4)  */
     uint32_t warps_per_cta;/* 1..8 (0 = 8)                                         */
     uint32_t ctas_per_sm;  /* resident blocks per SM (0 = as many as fit)          */
@@ -195,6 +196,12 @@ typedef struct {
     int32_t test_block;    /* tests only: index (in run-length order, longest
                               first) of a realisation whose waits can never
                               succeed, to exercise the timeout; -1 = none        */
+    uint32_t tile_y;       /* tile height for every realisation: 128 or 256
+                              (256 needs every L >= 256). 0: 128, or, with
+                              autotune, the faster of the two on the probe. The
+                              tile shape is part of the schedule (Sec. 3.1): a
+                              member equals the single-lattice run with the same
+                              tile shape (kpz_opts.by), bit for bit            */
 } kpz_batch_opts;
 
 typedef struct {
@@ -203,6 +210,7 @@ typedef struct {
     uint64_t items;                                  /* work items in the queue       */
     uint32_t n_probe;                                /* autotune probes timed         */
     double probe_ms[8];                              /* their times                   */
+    uint32_t tile_y;                                 /* tile height used (128, 256)   */
 } kpz_batch_info;
 
 /* Validate the specs (KPZ_EINVAL: bad L, p or q), allocate all lattices and

@@ -258,14 +258,14 @@ class kpz_batch_opts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("n_samples", ctypes.c_uint32), ("autotune", ctypes.c_int),
                 ("run", ctypes.c_uint32), ("warps_per_cta", ctypes.c_uint32),
                 ("ctas_per_sm", ctypes.c_uint32), ("timeout_ms", ctypes.c_uint32),
-                ("test_block", ctypes.c_int32)]
+                ("test_block", ctypes.c_int32), ("tile_y", ctypes.c_uint32)]
 
 
 class kpz_batch_info(ctypes.Structure):
     _fields_ = [("run", ctypes.c_uint32), ("warps_per_cta", ctypes.c_uint32),
                 ("ctas_per_sm", ctypes.c_uint32), ("grid", ctypes.c_uint32), ("graph", ctypes.c_int),
                 ("items", ctypes.c_uint64), ("n_probe", ctypes.c_uint32),
-                ("probe_ms", ctypes.c_double * 8)]
+                ("probe_ms", ctypes.c_double * 8), ("tile_y", ctypes.c_uint32)]
 
 
 def _bind_batch(L):
@@ -289,7 +289,7 @@ class Batch:
     persistent launch; results match single Lattice runs bit for bit."""
 
     def __init__(self, specs, n_samples=0, autotune=False, run=0, warps_per_cta=0, ctas_per_sm=0,
-                 timeout_ms=0, test_block=-1, stream=None):
+                 timeout_ms=0, test_block=-1, stream=None, tile_y=0):
         lib = load()
         if not hasattr(lib, "_batch_bound"):
             _bind_batch(lib)
@@ -309,6 +309,7 @@ class Batch:
         o.stream = stream or None
         o.n_samples, o.autotune, o.run = n_samples, int(bool(autotune)), run
         o.warps_per_cta, o.ctas_per_sm, o.timeout_ms, o.test_block = warps_per_cta, ctas_per_sm, timeout_ms, test_block
+        o.tile_y = tile_y
         self._b = ctypes.c_void_p()
         check(lib.kpz_batch_create(ctypes.byref(self._b), arr, len(self.specs), ctypes.byref(o)))
 
@@ -347,7 +348,7 @@ class Batch:
         check(load().kpz_batch_get_info(self._b, ctypes.byref(i)))
         return {"run": i.run, "warps_per_cta": i.warps_per_cta, "ctas_per_sm": i.ctas_per_sm,
                 "grid": i.grid, "graph": bool(i.graph), "items": i.items,
-                "probe_ms": list(i.probe_ms)[:i.n_probe]}
+                "probe_ms": list(i.probe_ms)[:i.n_probe], "tile_y": i.tile_y}
 
     def close(self):
         if getattr(self, "_b", None):

@@ -163,15 +163,19 @@ __device__ void band_sums(const SweepParams& P, const uint32_t* tl, uint32_t k, 
 
 // Per-warp shared memory. 16-byte aligned size: the slab copies are 16-byte
 // cp.async writes, so every warp's slot must start on a 16-byte boundary.
+template <int CR>
 struct alignas(16) WarpSlot {
-  run::WarpStage<1> stage;
+  run::WarpStage<CR> stage;
   SweepParams P;
 };
-static_assert(sizeof(WarpSlot) % 16 == 0, "warp slots must keep 16-byte alignment");
+static_assert(sizeof(WarpSlot<1>) % 16 == 0 && sizeof(WarpSlot<2>) % 16 == 0,
+              "warp slots must keep 16-byte alignment");
 
+// CR = cell rows per lane: tiles of 128 x 128 CR sites.
+template <int CR>
 __global__ void __launch_bounds__(256, 2) batch_kernel(const __grid_constant__ Plan Q) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  WarpSlot& ws = reinterpret_cast<WarpSlot*>(smem_raw)[threadIdx.x >> 5];
+  WarpSlot<CR>& ws = reinterpret_cast<WarpSlot<CR>*>(smem_raw)[threadIdx.x >> 5];
   __shared__ uint32_t tab[w2::kRunTableWords];   // W^2 run table (kpz_w2.cuh)
   w2::fill_run_table(tab);
   const uint32_t lane = threadIdx.x & 31u;
@@ -245,8 +249,8 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(const __grid_constant__ P
       // Device layer: this sweep's random tile origin (Sec. 3).
       const uint4 o = philox(kTagOrigin << 28, 0u, g, ws.P.sample, ws.P.k0, ws.P.k1);
       const uint32_t L = ws.P.g.L, ox = o.x & (L - 1u), oy = o.y & (L - 1u);
-      if (general) run::sweep_run<true, 1, false, true>(ws.P, ws.stage, nullptr, lane, g, ox, oy, ty, tx0, ws.P.run);
-      else         run::sweep_run<false, 1, false, true>(ws.P, ws.stage, nullptr, lane, g, ox, oy, ty, tx0, ws.P.run);
+      if (general) run::sweep_run<true, CR, false, true>(ws.P, ws.stage, nullptr, lane, g, ox, oy, ty, tx0, ws.P.run);
+      else         run::sweep_run<false, CR, false, true>(ws.P, ws.stage, nullptr, lane, g, ox, oy, ty, tx0, ws.P.run);
     }
     __threadfence();
     __syncwarp();
@@ -272,6 +276,7 @@ struct kpz_batch {
   uint32_t sms = 0;
   // knobs (execution only)
   uint32_t run_max = 4, wpc = 8, ctas_per_sm = 0, grid = 0;
+  uint32_t cr = 1;                   // cell rows per lane: tiles of 128 x 128 cr
   uint64_t timeout_ns = 10ull * 1000000000ull;
   int block = -1;
   // device memory
@@ -328,7 +333,7 @@ HostPlan build_plan(kpz_batch* b, std::vector<Real>& real) {
     uint32_t run = 1;
     while (run * 2 <= std::min(b->run_max, ntx)) run *= 2;
     r.P.ntx = ntx;
-    r.P.nty = ntx;
+    r.P.nty = r.P.g.L / (kTile * b->cr);
     r.P.run = run;
     r.P.runs_x = ntx / run;
     r.n_items = r.P.runs_x * r.P.nty;
@@ -427,7 +432,12 @@ PoolMap map_pool(const kpz_batch* b) {
   return m;
 }
 
-size_t smem_bytes(uint32_t wpc) { return wpc * sizeof(WarpSlot); }
+size_t smem_bytes(uint32_t wpc, uint32_t cr) {
+  return wpc * (cr == 2 ? sizeof(WarpSlot<2>) : sizeof(WarpSlot<1>));
+}
+const void* kernel_of(uint32_t cr) {
+  return cr == 2 ? (const void*)batch_kernel<2> : (const void*)batch_kernel<1>;
+}
 
 // Upload the plan for the current knobs; fills b->plan and b->grid.
 kpz_status prepare(kpz_batch* b, const std::vector<uint64_t>* cap_T) {
@@ -479,8 +489,8 @@ kpz_status prepare(kpz_batch* b, const std::vector<uint64_t>* cap_T) {
   b->real = real;
   if (cap_T) { b->spec = saved; b->times = saved_times; Q.nG = (uint32_t)b->times.size(); }
   int maxb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxb, batch_kernel, (int)(b->wpc * 32),
-                                                    smem_bytes(b->wpc)) != cudaSuccess || maxb < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxb, kernel_of(b->cr), (int)(b->wpc * 32),
+                                                    smem_bytes(b->wpc, b->cr)) != cudaSuccess || maxb < 1)
     return KPZ_ECUDA;
   const uint32_t per_sm = b->ctas_per_sm ? std::min<uint32_t>(b->ctas_per_sm, (uint32_t)maxb) : (uint32_t)maxb;
   b->grid = per_sm * b->sms;
@@ -497,8 +507,8 @@ cudaError_t enqueue(kpz_batch* b, bool capturing = false) {
   if (e == cudaSuccess) e = cudaMemsetAsync(m.sweep_done, 0, (char*)(m.err + 64) - (char*)m.sweep_done, st);
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&b->plan};
-  e = cudaLaunchCooperativeKernel((const void*)batch_kernel, dim3(b->grid), dim3(b->wpc * 32), args,
-                                  smem_bytes(b->wpc), st);
+  e = cudaLaunchCooperativeKernel(kernel_of(b->cr), dim3(b->grid), dim3(b->wpc * 32), args,
+                                  smem_bytes(b->wpc, b->cr), st);
   if (!capturing) count_launch();
   return e;
 }
@@ -535,6 +545,10 @@ kpz_status kpz_batch_create(kpz_batch** out, const kpz_spec* specs, uint32_t n, 
       return KPZ_EINVAL;
   }
   if (o.warps_per_cta > 8 || (o.run & (o.run - 1)) != 0 || o.n_samples > 1024) return KPZ_EINVAL;
+  if (o.tile_y != 0 && o.tile_y != kTile && o.tile_y != 2u * kTile) return KPZ_EINVAL;
+  uint32_t Lmin = ~0u;
+  for (uint32_t c = 0; c < n; ++c) Lmin = std::min(Lmin, specs[c].L);
+  if (o.tile_y == 2u * kTile && Lmin < 2u * kTile) return KPZ_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return KPZ_ENODEV;
   kpz_batch* b = new (std::nothrow) kpz_batch();
@@ -555,8 +569,11 @@ kpz_status kpz_batch_create(kpz_batch** out, const kpz_spec* specs, uint32_t n, 
   b->ctas_per_sm = o.ctas_per_sm;
   b->timeout_ns = (uint64_t)(o.timeout_ms ? o.timeout_ms : 10000u) * 1000000ull;
   b->block = o.test_block;
-  if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem_bytes(8)) != cudaSuccess)
+  b->cr = o.tile_y == 2u * kTile ? 2u : 1u;
+  if (cudaFuncSetAttribute(kernel_of(1), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem_bytes(8, 1)) != cudaSuccess ||
+      cudaFuncSetAttribute(kernel_of(2), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem_bytes(8, 2)) != cudaSuccess)
     return fail_free(b, KPZ_ECUDA);
   kpz_status st = allocate(b);
   if (st) return fail_free(b, st);
@@ -581,6 +598,23 @@ kpz_status kpz_batch_create(kpz_batch** out, const kpz_spec* specs, uint32_t n, 
         if (b->nprobe < 64) b->probe_ms[b->nprobe++] = ms;
         if (ms < best) { best = ms; best_run = rr; best_wpc = ww; }
       }
+    // Tile height (part of the schedule, so only when the caller leaves it
+    // open): 128 x 256 at the best run length, both block sizes.
+    uint32_t best_cr = b->cr;
+    if (o.tile_y == 0 && Lmin >= 2u * kTile) {
+      b->cr = 2;
+      for (uint32_t ww : wpcs) {
+        b->run_max = best_run; b->wpc = ww; b->ctas_per_sm = 0;
+        st = prepare(b, &cap);
+        if (st) return fail_free(b, st);
+        float ms = 0.f;
+        st = run_once(b, &ms);
+        if (st) return fail_free(b, st);
+        if (b->nprobe < 64) b->probe_ms[b->nprobe++] = ms;
+        if (ms < best) { best = ms; best_wpc = ww; best_cr = 2; }
+      }
+    }
+    b->cr = best_cr;
     b->run_max = best_run;
     b->wpc = best_wpc;
   }
@@ -700,8 +734,9 @@ kpz_status kpz_batch_get_info(const kpz_batch* b, kpz_batch_info* out) {
   out->ctas_per_sm = b->grid / (b->sms ? b->sms : 1);
   out->graph = b->graph;
   out->items = b->plan.total;
-  out->n_probe = b->nprobe;
+  out->n_probe = std::min<uint32_t>(b->nprobe, 8);
   for (uint32_t k = 0; k < 8; ++k) out->probe_ms[k] = k < b->nprobe ? b->probe_ms[k] : 0.0;
+  out->tile_y = kTile * b->cr;
   return KPZ_OK;
 }
 

@@ -20,8 +20,8 @@ def eng():
     return engine()
 
 
-def _single(eng, L, p, q, seed, sample, n, times):
-    lat = eng.Lattice(L, p, q, seed=seed, sample=sample)
+def _single(eng, L, p, q, seed, sample, n, times, tile_y=0):
+    lat = eng.Lattice(L, p, q, seed=seed, sample=sample, tile_y=tile_y)
     out, t0 = {}, 0
     for t in times:
         if t > n:
@@ -103,3 +103,41 @@ def test_wait_that_never_succeeds_times_out(eng):
     ok = eng.Batch(SPECS[:2], n_samples=4)      # the device stays usable
     ok.run()
     ok.close()
+
+
+SPECS_TALL = [(256, 1.0, 0.0, 1, 0, 14), (512, 0.8, 0.2, 7, 3, 9), (1024, 0.95, 0.05, 2, 1, 4),
+              (256, 0.5, 0.5, 3, 2, 11)]
+
+
+def test_tall_tile_batch_matches_single_lattice_runs(eng):
+    """128 x 256 tiles in the batch give the single-lattice 128 x 256 schedule."""
+    b = eng.Batch(SPECS_TALL, n_samples=6, tile_y=256)
+    assert b.info()["tile_y"] == 256
+    b.run()
+    times = [int(t) for t in b.times()]
+    s1, s2, h00 = b.sums()
+    for i, spec in enumerate(SPECS_TALL):
+        ref = _single(eng, *spec, times, tile_y=256)
+        for k, t in enumerate(times):
+            if t <= spec[5]:
+                assert (int(s1[i, k]), s2[i, k]) == ref[t][:2], (spec, t)
+        assert h00[i] == ref[spec[5]][2]
+    b.close()
+
+
+def test_autotuned_tile_shape_is_reported_and_reproducible(eng):
+    from paper_1204_5072_gb300._lib import KPZ_EINVAL, KpzError
+    b = eng.Batch(SPECS_TALL, n_samples=6, autotune=True)
+    info = b.info()
+    assert info["tile_y"] in (128, 256) and len(info["probe_ms"]) == 8
+    b.run()
+    got = b.sums()
+    b.close()
+    fixed = eng.Batch(SPECS_TALL, n_samples=6, tile_y=info["tile_y"])
+    fixed.run()
+    ref = fixed.sums()
+    fixed.close()
+    assert all(np.array_equal(a, c) for a, c in zip(got, ref))
+    with pytest.raises(KpzError) as e:   # 128 x 256 tiles need L >= 256
+        eng.Batch([(128, 1.0, 0.0, 1, 0, 3)], tile_y=256)
+    assert e.value.status == KPZ_EINVAL
