@@ -172,6 +172,18 @@ def cpu_baseline(L_full: int, mcs_sample: int):
             "seconds": dt}
 
 
+def job_config(L, mcs, world):
+    """The `config` of the benchmark job (both arms report the same one)."""
+    w = I.L65536_2000
+    n = len(I.sample_times(mcs))
+    return {"workload": f"octahedron KPZ L={L} p=1 q=0 {mcs} MCS, W^2 at "
+                        f"{n} log-spaced times, 1 realisation per GPU",
+            "L": L, "p": w.p, "q": w.q, "mcs": mcs, "samples": n,
+            "tile": "128x128, 4x4 cells", "seed": w.seed,
+            "l2": "lattice (L^2/8 bytes = 512 MiB at L=2^16) larger than L2",
+            "parallelism": f"replicas{world}"}
+
+
 def run_reference(a):
     """--impl reference: the CPU oracle timed on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
@@ -196,8 +208,7 @@ def run_reference(a):
             "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1e3 * dt / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic (flat checkerboard start)",
-            "config": {"workload": f"octahedron KPZ L={a.L} p=1 q=0 {a.mcs} MCS (CPU oracle sample)",
-                       "L": a.L, "mcs": a.mcs},
+            "config": job_config(a.L, a.mcs, a.gpus),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -460,11 +471,7 @@ def main():
                 "warmup": max(a.warmup, 3), "ms_per_step": 1e3 * elapsed / a.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
                 "data": "synthetic (flat checkerboard start, p=1 q=0)",
-                "config": {"workload": f"octahedron KPZ L={L} p=1 q=0 {mcs} MCS, W^2 at "
-                                       f"{len(times)} log-spaced times, 1 realisation per GPU",
-                           "L": L, "p": w.p, "q": w.q, "mcs": mcs, "samples": len(times),
-                           "tile": "128x128, 4x4 cells", "seed": w.seed,
-                           "l2": "lattice (L^2/8 bytes = 512 MiB at L=2^16) larger than L2", "parallelism": f"replicas{world}"},
+                "config": job_config(L, mcs, world),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk.summary(), "gpu_launches": launches,
                 "w2_final": rough[-1]["w2"], "batch": batch, "surrogate": sur}

@@ -221,7 +221,7 @@ __device__ __forceinline__ void sweep_run(const SweepParams& P, WarpStage<CR>& w
 
     // Write back block column t and slide the window to tile t+1.
     cp_async_wait();
-    if (!kGeneral && CR == 1 && t != 0u && !last) {
+    if (!kGeneral && t != 0u && !last) {
       // Interior tile: both words of each window row are this run's alone.
 #pragma unroll
       for (uint32_t xq = 0; xq < 4; ++xq) {
