@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--cpu-sample-mcs", type=int, default=100)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-cap", type=int, default=200)
+    ap.add_argument("--batch-n", type=int, default=512)
+    ap.add_argument("--batch-only", action="store_true",
+                    help="profiling aid: run only the batched-ensemble section (no comparisons)")
     ap.add_argument("--no-surrogate", action="store_true")
     return ap.parse_args()
 
@@ -70,7 +73,7 @@ ALU_LANES_PER_SM = 64   # integer logic pipe: 16 lanes per SM sub-partition per 
 
 
 # Files the sweep kernel is compiled from (their hash ties a profile to the source).
-SWEEP_SOURCES = ("kpz_sweep.cu", "kpz_rounds.cuh", "kpz_common.cuh", "kpz_internal.h")
+SWEEP_SOURCES = ("kpz_sweep.cu", "kpz_run.cuh", "kpz_rounds.cuh", "kpz_common.cuh", "kpz_internal.h")
 
 
 def sweep_source_sha():
@@ -216,13 +219,13 @@ def run_reference(a):
 
 
 # --------------------------------------------------------------------------- #
-def batch_bench(eng, cap, seed=1):
+def batch_bench(eng, cap, seed=1, n_specs=512, compare=True):
     """Batched ensemble (512 realisations shaped like the batched workload: L =
     2^{8..13} log-uniform, p ~ U[0.5, 1], q = 1 - p, run length min(4 L^1.6, cap)),
     one persistent graph launch, against (i) one launch per sweep per realisation
     (kpz_run, W^2 at the same times) and (ii) one persistent launch per realisation."""
     import torch
-    specs = [(s.L, s.p, s.q, seed, s.sample, min(s.mcs, cap)) for s in I.ensemble_specs(512, seed=seed)]
+    specs = [(s.L, s.p, s.q, seed, s.sample, min(s.mcs, cap)) for s in I.ensemble_specs(n_specs, seed=seed)]
     attempts = float(sum(L * L * n for L, _, _, _, _, n in specs))
     t0 = time.perf_counter()
     b = eng.Batch(specs, n_samples=64, autotune=True)
@@ -236,6 +239,15 @@ def batch_bench(eng, cap, seed=1):
     times = [int(t) for t in b.times()]
     info = b.info()
     b.close()
+    n = len(specs)
+    out = {"metric": "batched realisations/s", "value": n / batched, "unit": "realisations/s",
+           "attempts_per_s": attempts / batched, "seconds": batched,
+           "workload": f"{n} realisations, L=2^(8..13) log-uniform, p~U[0.5,1], q=1-p, "
+                       f"T=min(4 L^1.6, {cap}) MCS, W^2 at the common log-spaced times (seed {seed})",
+           "tuning": {k: info[k] for k in ("run", "warps_per_cta", "ctas_per_sm", "grid", "graph", "tile_y")},
+           "autotune_s": create_s}
+    if not compare:
+        return out
     t0 = time.perf_counter()
     for (L, p, q, sd, smp, n) in specs:
         lat = eng.Lattice(L, p, q, seed=sd, sample=smp)
@@ -256,16 +268,10 @@ def batch_bench(eng, cap, seed=1):
         one.close()
     per_real = time.perf_counter() - t0
     n = len(specs)
-    return {"metric": "batched realisations/s", "value": n / batched, "unit": "realisations/s",
-            "attempts_per_s": attempts / batched, "seconds": batched,
-            "vs_launch_per_sweep": {"value": n / per_sweep, "seconds": per_sweep,
-                                    "speedup": per_sweep / batched},
-            "vs_launch_per_realisation": {"value": n / per_real, "seconds": per_real,
-                                          "speedup": per_real / batched},
-            "workload": f"512 realisations, L=2^(8..13) log-uniform, p~U[0.5,1], q=1-p, "
-                        f"T=min(4 L^1.6, {cap}) MCS, W^2 at the common log-spaced times (seed {seed})",
-            "tuning": {k: info[k] for k in ("run", "warps_per_cta", "ctas_per_sm", "grid", "graph", "tile_y")},
-            "autotune_s": create_s}
+    out["vs_launch_per_sweep"] = {"value": n / per_sweep, "seconds": per_sweep, "speedup": per_sweep / batched}
+    out["vs_launch_per_realisation"] = {"value": n / per_real, "seconds": per_real,
+                                        "speedup": per_real / batched}
+    return out
 
 
 def surrogate_bench(eng):
@@ -342,6 +348,10 @@ def main():
     __graft_entry__.build()
     import paper_1204_5072_gb300 as eng
     from paper_1204_5072_gb300._lib import launch_count
+    if a.batch_only:   # profiling aid: the batched-ensemble section alone
+        if rank == 0:
+            print(json.dumps(batch_bench(eng, a.batch_cap, n_specs=a.batch_n, compare=False)), flush=True)
+        return
 
     w = I.L65536_2000
     L, mcs = a.L, a.mcs
@@ -463,7 +473,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         cpu = cpu_baseline(L, a.cpu_sample_mcs)
-    batch = None if (a.no_batch or world > 1) else batch_bench(eng, a.batch_cap)
+    batch = None if (a.no_batch or world > 1) else batch_bench(eng, a.batch_cap, n_specs=a.batch_n)
     sur = None if (a.no_surrogate or world > 1) else surrogate_bench(eng)
 
     if rank == 0:
