@@ -175,6 +175,27 @@ def cpu_baseline(L_full: int, mcs_sample: int):
             "seconds": dt}
 
 
+def replica_sample(rank: int) -> int:
+    """The realisation a rank runs under torchrun: sample = rank, i.e. its own
+    Philox streams (the path has no exchange step; replicas only)."""
+    return rank
+
+
+def max_over_ranks(seconds: float, dist=None, device="cuda") -> float:
+    """The slowest rank's time (the job ends when every rank has finished)."""
+    if dist is None:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world: int, steps: int, mcs: int, L: int, seconds: float) -> float:
+    """Attempts/s of the whole job: every rank sweeps its own L x L lattice."""
+    return float(world) * steps * mcs * L * L / seconds
+
+
 def job_config(L, mcs, world):
     """The `config` of the benchmark job (both arms report the same one)."""
     w = I.L65536_2000
@@ -357,7 +378,7 @@ def main():
     L, mcs = a.L, a.mcs
     times = I.sample_times(mcs)
     stream = torch.cuda.current_stream()
-    lat = eng.Lattice(L, w.p, w.q, seed=w.seed, sample=rank)
+    lat = eng.Lattice(L, w.p, w.q, seed=w.seed, sample=replica_sample(rank))
 
     sweep_events = []  # (start, end, n_sweeps) on the engine's stream
 
@@ -398,13 +419,9 @@ def main():
         t_end.record(stream)
         torch.cuda.synchronize()
     launches = launch_count() - launches0
-    elapsed = t_start.elapsed_time(t_end) / 1e3
-    if dist:
-        tt = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
+    elapsed = max_over_ranks(t_start.elapsed_time(t_end) / 1e3, dist)
     attempts = float(world) * a.steps * mcs * L * L
-    value = attempts / elapsed
+    value = whole_job_value(world, a.steps, mcs, L, elapsed)
     sweep_ms = sum(e0.elapsed_time(e1) for e0, e1, _ in sweep_events)
     n_sweeps = sum(n for _, _, n in sweep_events)
     per_sweep_s = sweep_ms / 1e3 / n_sweeps
@@ -462,11 +479,7 @@ def main():
         for _ in range(a.steps):
             e2e_step()
         barrier()
-        e2e_dt = time.perf_counter() - t0
-        if dist:
-            tt = torch.tensor([e2e_dt], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_dt = float(tt.item())
+        e2e_dt = max_over_ranks(time.perf_counter() - t0, dist)
         e2e = {"value": attempts / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": nwords * 4,
                "d2h_bytes_per_step": nwords * 4 + len(times) * 48}
 
