@@ -208,6 +208,31 @@ def job_config(L, mcs, world):
             "parallelism": f"replicas{world}"}
 
 
+def cpu_all_cores(mcs_sample: int):
+    """The oracle with the tiles of each sweep spread over every host core
+    (bit-identical to the serial oracle), on the same L = 1024 sub-run."""
+    from oracle import oracle as O
+    L, w = 1024, I.L65536_2000
+    cores = os.cpu_count() or 1
+    st = O.State.flat(L)
+    t0 = time.perf_counter()
+    st.run_threads(mcs_sample, w.bx, w.by, w.p, w.q, w.seed, w.sample, threads=cores)
+    st.w2()
+    dt = time.perf_counter() - t0
+    return {"value": mcs_sample * L * L / dt, "unit": UNIT, "cores": cores,
+            "kind": "oracle, tiles of a sweep over all host threads",
+            "sample": f"L={L}, {mcs_sample} MCS from the flat start + W^2", "seconds": dt}
+
+
+# The paper's own update rates (order of magnitude from its text; its figures
+# are not available): context for the GB300 numbers, not a target.
+PAPER_CONTEXT = {"gpu_updates_per_s": 1e9,
+                 "gpu_hardware": "Tesla C1060, Fermi C2050/C2070, Radeon HD5970/HD6970",
+                 "cpu_updates_per_s": 1e7,
+                 "cpu_hardware": "Opteron F8380, Core i5 430M, Core i7 920 (one core)",
+                 "workload": "p = 1, q = 0, bit-coded lattice (Sec. 4)"}
+
+
 def run_reference(a):
     """--impl reference: the CPU oracle timed on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
@@ -483,9 +508,10 @@ def main():
         e2e = {"value": attempts / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": nwords * 4,
                "d2h_bytes_per_step": nwords * 4 + len(times) * 48}
 
-    cpu = None
+    cpu = cpu_mt = None
     if rank == 0 and world == 1 and not a.no_cpu:
         cpu = cpu_baseline(L, a.cpu_sample_mcs)
+        cpu_mt = cpu_all_cores(max(10, a.cpu_sample_mcs // 2))
     batch = None if (a.no_batch or world > 1) else batch_bench(eng, a.batch_cap, n_specs=a.batch_n)
     sur = None if (a.no_surrogate or world > 1) else surrogate_bench(eng)
 
@@ -495,7 +521,8 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
                 "data": "synthetic (flat checkerboard start, p=1 q=0)",
                 "config": job_config(L, mcs, world),
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "cpu_baseline": cpu, "cpu_all_cores": cpu_mt,
+                "paper_context": PAPER_CONTEXT, "e2e": e2e,
                 "clocks": clk.summary(), "gpu_launches": launches,
                 "w2_final": rough[-1]["w2"], "batch": batch, "surrogate": sur}
         print(json.dumps(line), flush=True)

@@ -333,6 +333,40 @@ int orc_flat_tile_sweep(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint3
     return 0;
 }
 
+/* The same sweep with the tiles spread over nthreads OpenMP threads (natural
+ * order inside each tile). Tiles of one sweep read and write disjoint slopes
+ * (dead border, Sec. 3), so the result equals orc_sweep's bit for bit; used
+ * to time the oracle on all host cores. Returns 0, or -1 on bad input. */
+int orc_sweep_threads(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32_t Tq,
+                      uint64_t seed, uint32_t sample, uint32_t s,
+                      uint8_t* sx, uint8_t* sy, int64_t* h00, int nthreads) {
+    if (L < 4 || (L & (L - 1)) || Bx < 4 || By < 4 || (Bx & (Bx - 1)) || (By & (By - 1)) ||
+        Bx > L || By > L || Tp > 65536u || Tq > 65536u || nthreads < 1)
+        return -1;
+    orc_params P = {L, Bx, By, Tp, Tq, sample, seed};
+    uint32_t w[4];
+    philox_at((uint32_t)TAG_ORIGIN << 28, 0, s, sample, seed, w);
+    uint32_t ox = w[0] & (L - 1), oy = w[1] & (L - 1);
+    int64_t ntiles = (int64_t)(L / Bx) * (L / By);
+    uint32_t ncells = (Bx / 4) * (By / 4);
+    int64_t dh = 0;
+    int bad = 0;
+#pragma omp parallel num_threads(nthreads) reduction(+ : dh) reduction(| : bad)
+    {
+        uint32_t* cell_order = (uint32_t*)malloc(sizeof(uint32_t) * ncells);
+        memo mpos = {0}, macc[4] = {{0}};
+        if (!cell_order) bad = 1;
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t T = 0; T < ntiles; ++T)
+            if (cell_order)
+                tile_rounds(&P, s, (uint32_t)T, ox, oy, 16, 0, cell_order, &mpos, macc, sx, sy, NULL, &dh);
+        free(cell_order);
+    }
+    if (bad) return -1;
+    if (h00) *h00 += dh;
+    return 0;
+}
+
 /* n sweeps s = t0 .. t0+n-1 in natural order. */
 int orc_run(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32_t Tq,
             uint64_t seed, uint32_t sample, uint32_t t0, uint32_t n,

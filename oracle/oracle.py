@@ -30,7 +30,11 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        base = ["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, _SRC]
+        try:   # OpenMP only spreads tiles over threads (orc_sweep_threads); results do not change
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _SO)
     return _SO
 
@@ -73,6 +77,10 @@ def lib():
                                               c.POINTER(c.c_uint32), c.POINTER(c.c_uint32),
                                               c.POINTER(c.c_int64)]
             L.orc_flat_tile_sweep.restype = c.c_int
+            L.orc_sweep_threads.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32,
+                                            c.c_uint64, c.c_uint32, c.c_uint32, u8p, u8p,
+                                            c.POINTER(c.c_int64), c.c_int]
+            L.orc_sweep_threads.restype = c.c_int
             _lib = L
     return _lib
 
@@ -135,6 +143,20 @@ class State:
             raise ValueError("invalid oracle parameters")
         self.h00 = h.value
         self.t = s + 1
+        return self
+
+    def run_threads(self, n, Bx, By, p, q, seed, sample=0, threads=None):
+        """n sweeps with the tiles of each sweep spread over `threads` host
+        threads (default: all cores); same result as run()."""
+        threads = threads or os.cpu_count() or 1
+        h = ctypes.c_int64(self.h00)
+        for _ in range(n):
+            rc = lib().orc_sweep_threads(self.L, Bx, By, threshold(p), threshold(q), seed, sample, self.t,
+                                         self.sx, self.sy, ctypes.byref(h), threads)
+            if rc:
+                raise ValueError("bad schedule parameters")
+            self.t += 1
+        self.h00 = h.value
         return self
 
     def run(self, n, Bx, By, p, q, seed, sample=0):

@@ -8,7 +8,7 @@ simulator produces, by the library's own forward, backward and Adam kernels.
 Its curves give the saturation time t_x(L, p, q): the time the predicted
 log W^2 comes within `sat_tol` of its plateau. The batcher can then run each
 realisation for `factor * t_x` sweeps instead of a fixed rule such as
-4 L^1.6; the plain simulation stays the fallback and the judge of the error.
+4 L^1.6; the plain simulation stays the fallback and the measure of the error.
 """
 from __future__ import annotations
 

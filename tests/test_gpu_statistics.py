@@ -6,7 +6,8 @@ the decomposition must not change the physics).
 * Random-sequential reference: the ensemble mean of W^2(t) from the GPU
   agrees with the oracle's random-sequential-update runs (no decomposition)
   within the early-time offset of single-hit double tiling (about 3-5 % for
-  t <= 64) and within errors later.
+  t <= 64, measured with the oracle at L = 128-256 for tile sizes 16-128) and
+  within errors later.
 * lambda = 0 (p = q): Edwards-Wilkinson class, much slower (logarithmic) growth.
 """
 import numpy as np

@@ -188,3 +188,13 @@ def test_flat_tile_windows_assemble_the_full_sweep(L, Bx, By, p, q, seed, sample
         dh += d
     assert np.array_equal(sx, st.sx.reshape(L, L)) and np.array_equal(sy, st.sy.reshape(L, L))
     assert dh == st.h00
+
+
+@pytest.mark.parametrize("L,Bx,By,p,q", [(256, 32, 32, 1.0, 0.0), (256, 64, 128, 0.8, 0.3), (512, 128, 128, 0.95, 0.05)])
+def test_threaded_tiles_give_the_serial_sweep(L, Bx, By, p, q):
+    """Tiles of one sweep commute (dead border, Sec. 3): the OpenMP tile loop
+    reproduces the serial sweep bit for bit, h(0,0) included."""
+    a = O.State.flat(L).run(5, Bx, By, p, q, 3, 1)
+    b = O.State.flat(L).run_threads(5, Bx, By, p, q, 3, 1, threads=4)
+    assert np.array_equal(a.sx, b.sx) and np.array_equal(a.sy, b.sy)
+    assert (a.h00, a.t) == (b.h00, b.t)
