@@ -41,6 +41,9 @@
  *     level n uses bit b of A_{n>>2}[n&3];  U = sum_n bit << (15-n)
  *   a minimum flips iff U < Tp, a maximum flips iff U < Tq,
  *   Tp = min(65536, floor(p*65536 + 0.5)), likewise Tq.
+ * Tile-set variant (orc_sweep_tilesets): same origin and tiles, no dead border,
+ * the four sets (tx & 1) + 2 (ty & 1) swept in an order drawn from
+ * philox(5<<28, 0, s, sample) (orc_tileset_order).
  * Random-sequential reference (no decomposition), attempt a of sweep s:
  *   w = philox(4<<28 | (a>>32), a & 0xffffffff, s, sample)
  *   site (w0 & (L-1), w1 & (L-1)), U = w2 >> 16.
@@ -88,7 +91,7 @@ static void philox_at(uint32_t tag_index, uint32_t c1, uint32_t s, uint32_t samp
     orc_philox(ctr, key, out);
 }
 
-enum { TAG_ORIGIN = 0, TAG_SET = 1, TAG_POS = 2, TAG_ACC = 3, TAG_RSU = 4 };
+enum { TAG_ORIGIN = 0, TAG_SET = 1, TAG_POS = 2, TAG_ACC = 3, TAG_RSU = 4, TAG_PHASE = 5 };
 
 /* ------------------------------------------------------------------------- */
 /* Model (Sec. 2.1).                                                          */
@@ -146,6 +149,7 @@ int orc_attempt(uint32_t L, uint8_t* sx, uint8_t* sy, uint32_t i, uint32_t j,
 typedef struct {
     uint32_t L, Bx, By, Tp, Tq, sample;
     uint64_t seed;
+    int live_border;   /* 1: no dead border (tile-set variant); 0: the paper's dead border */
 } orc_params;
 
 /* One-entry memo of the last Philox block, so that the 32 cells that share a
@@ -240,7 +244,7 @@ static void tile_rounds(const orc_params* P, uint32_t s, uint32_t T, uint32_t ox
             position_bits(P, mpos, T, s, cx, cy, r, &xi, &yi);
             uint32_t u = 4 * cx + 2 * qx + xi;
             uint32_t v = 4 * cy + 2 * qy + yi;
-            if (u == 0 || v == 0) continue;          /* dead border of the tile */
+            if (!P->live_border && (u == 0 || v == 0)) continue;   /* dead border of the tile */
             uint32_t i = (x0 + u) & (L - 1), j = (y0 + v) & (L - 1);
             uint32_t U = acceptance_number(P, macc, T, s, cx, cy, r);
             int dh;
@@ -271,7 +275,7 @@ int orc_sweep(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32_t Tq,
     if (L < 4 || (L & (L - 1)) || Bx < 4 || By < 4 || (Bx & (Bx - 1)) || (By & (By - 1)) ||
         Bx > L || By > L || Tp > 65536u || Tq > 65536u)
         return -1;
-    orc_params P = {L, Bx, By, Tp, Tq, sample, seed};
+    orc_params P = {L, Bx, By, Tp, Tq, sample, seed, 0};
 
     /* Device layer: the origin of the tile grid moves to a random site each sweep. */
     uint32_t w[4];
@@ -311,7 +315,7 @@ int orc_flat_tile_sweep(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint3
     if (L < 4 || (L & (L - 1)) || Bx < 4 || By < 4 || (Bx & (Bx - 1)) || (By & (By - 1)) ||
         Bx > L || By > L || Tp > 65536u || Tq > 65536u || T >= (L / Bx) * (L / By))
         return -1;
-    orc_params P = {L, Bx, By, Tp, Tq, sample, seed};
+    orc_params P = {L, Bx, By, Tp, Tq, sample, seed, 0};
     uint32_t w[4];
     philox_at((uint32_t)TAG_ORIGIN << 28, 0, s, sample, seed, w);
     uint32_t ox = w[0] & (L - 1), oy = w[1] & (L - 1);
@@ -343,7 +347,7 @@ int orc_sweep_threads(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32_
     if (L < 4 || (L & (L - 1)) || Bx < 4 || By < 4 || (Bx & (Bx - 1)) || (By & (By - 1)) ||
         Bx > L || By > L || Tp > 65536u || Tq > 65536u || nthreads < 1)
         return -1;
-    orc_params P = {L, Bx, By, Tp, Tq, sample, seed};
+    orc_params P = {L, Bx, By, Tp, Tq, sample, seed, 0};
     uint32_t w[4];
     philox_at((uint32_t)TAG_ORIGIN << 28, 0, s, sample, seed, w);
     uint32_t ox = w[0] & (L - 1), oy = w[1] & (L - 1);
@@ -364,6 +368,61 @@ int orc_sweep_threads(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32_
     }
     if (bad) return -1;
     if (h00) *h00 += dh;
+    return 0;
+}
+
+/* Variant of the device layer (KMC-style double tiling, Sec. 3.2 describes it
+ * for the KMC model): the same random origin and Bx x By tiles, grouped into
+ * four sets by (tx mod 2, ty mod 2); the sets are swept one after the other in
+ * an order drawn per sweep, and there is no dead border: every site of a tile
+ * is live, and the neighbours it reads across the tile edge belong to tiles of
+ * other sets, which are idle meanwhile. Set order of sweep s:
+ *   w = philox(5<<28, 0, s, sample); perm = (0, 1, 2, 3);
+ *   for i = 3, 2, 1: swap perm[i] and perm[w[3-i] mod (i+1)]  (Fisher-Yates)
+ * and phase i sweeps set perm[i] = (tx & 1) + 2 (ty & 1). The work-group layer
+ * (16 single-hit rounds per tile) and its random streams are unchanged.
+ * order as in orc_sweep (tile and cell order inside a phase; no effect).
+ * Needs an even number of tiles per row and column. Returns 0, or -1. */
+int orc_tileset_order(uint32_t s, uint32_t sample, uint64_t seed, uint32_t perm[4]) {
+    uint32_t w[4];
+    philox_at((uint32_t)TAG_PHASE << 28, 0, s, sample, seed, w);
+    for (uint32_t i = 0; i < 4; ++i) perm[i] = i;
+    for (uint32_t i = 3; i >= 1; --i) {
+        uint32_t j = w[3 - i] % (i + 1), t = perm[i];
+        perm[i] = perm[j]; perm[j] = t;
+    }
+    return 0;
+}
+
+int orc_sweep_tilesets(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32_t Tq,
+                       uint64_t seed, uint32_t sample, uint32_t s,
+                       uint8_t* sx, uint8_t* sy, int64_t* h00, uint64_t order) {
+    if (L < 4 || (L & (L - 1)) || Bx < 4 || By < 4 || (Bx & (Bx - 1)) || (By & (By - 1)) ||
+        2 * Bx > L || 2 * By > L || Tp > 65536u || Tq > 65536u)
+        return -1;
+    orc_params P = {L, Bx, By, Tp, Tq, sample, seed, 1};
+    uint32_t w[4];
+    philox_at((uint32_t)TAG_ORIGIN << 28, 0, s, sample, seed, w);
+    uint32_t ox = w[0] & (L - 1), oy = w[1] & (L - 1);
+    uint32_t perm[4];
+    orc_tileset_order(s, sample, seed, perm);
+    uint32_t ntx = L / Bx, nty = L / By, ntiles = ntx * nty;
+    uint32_t ncells = (Bx / 4) * (By / 4);
+    uint32_t* tile_order = (uint32_t*)malloc(sizeof(uint32_t) * ntiles);
+    uint32_t* cell_order = (uint32_t*)malloc(sizeof(uint32_t) * ncells);
+    if (!tile_order || !cell_order) { free(tile_order); free(cell_order); return -1; }
+    shuffle(tile_order, ntiles, order >= 2 ? order : 0);
+    if (order == 1)
+        for (uint32_t n = 0; n < ntiles; ++n) tile_order[n] = ntiles - 1 - n;
+    memo mpos = {0}, macc[4] = {{0}};
+    for (uint32_t phase = 0; phase < 4; ++phase)
+        for (uint32_t n = 0; n < ntiles; ++n) {
+            uint32_t T = tile_order[n], tx = T % ntx, ty = T / ntx;
+            if ((tx & 1u) + 2u * (ty & 1u) != perm[phase]) continue;
+            tile_rounds(&P, s, T, ox, oy, 16, order, cell_order, &mpos, macc, sx, sy, NULL, h00);
+        }
+    free(tile_order);
+    free(cell_order);
     return 0;
 }
 

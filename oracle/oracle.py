@@ -81,6 +81,12 @@ def lib():
                                             c.c_uint64, c.c_uint32, c.c_uint32, u8p, u8p,
                                             c.POINTER(c.c_int64), c.c_int]
             L.orc_sweep_threads.restype = c.c_int
+            L.orc_sweep_tilesets.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32,
+                                             c.c_uint64, c.c_uint32, c.c_uint32, u8p, u8p,
+                                             c.POINTER(c.c_int64), c.c_uint64]
+            L.orc_sweep_tilesets.restype = c.c_int
+            L.orc_tileset_order.argtypes = [c.c_uint32, c.c_uint32, c.c_uint64, u32p]
+            L.orc_tileset_order.restype = c.c_int
             _lib = L
     return _lib
 
@@ -91,6 +97,13 @@ def philox(ctr, key) -> np.ndarray:
     out = np.zeros(4, np.uint32)
     lib().orc_philox(np.asarray(ctr, np.uint32), np.asarray(key, np.uint32), out)
     return out
+
+
+def tileset_order(s: int, sample: int, seed: int) -> list:
+    """Order in which the four tile sets are swept in sweep s (tile-set variant)."""
+    out = np.zeros(4, np.uint32)
+    lib().orc_tileset_order(s, sample, seed, out)
+    return [int(v) for v in out]
 
 
 def threshold(p: float) -> int:
@@ -143,6 +156,23 @@ class State:
             raise ValueError("invalid oracle parameters")
         self.h00 = h.value
         self.t = s + 1
+        return self
+
+    def sweep_tilesets(self, Bx, By, p, q, seed, sample=0, order=0):
+        """One sweep of the tile-set variant of the device layer (four sets of
+        tiles swept in a random order, no dead border)."""
+        h = ctypes.c_int64(self.h00)
+        rc = lib().orc_sweep_tilesets(self.L, Bx, By, threshold(p), threshold(q), seed, sample, self.t,
+                                      self.sx, self.sy, ctypes.byref(h), order)
+        if rc:
+            raise ValueError("invalid oracle parameters")
+        self.h00 = h.value
+        self.t += 1
+        return self
+
+    def run_tilesets(self, n, Bx, By, p, q, seed, sample=0):
+        for _ in range(n):
+            self.sweep_tilesets(Bx, By, p, q, seed, sample)
         return self
 
     def run_threads(self, n, Bx, By, p, q, seed, sample=0, threads=None):
