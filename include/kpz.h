@@ -74,6 +74,14 @@ typedef struct {
                              its scratch; at least kpz_device_bytes(L) bytes,
                              256-byte aligned                                        */
     size_t dev_bytes;     /* size of dev_buf                                        */
+    uint32_t decomposition; /* device layer: 0 = dead-border tiles with a random
+                             origin (Sec. 3, the paper's KPZ scheme); 1 = the
+                             double tiling the paper uses for KMC (Sec. 3.2):
+                             the same tiles in four sets (tx & 1) + 2 (ty & 1),
+                             swept one set at a time in an order drawn per sweep
+                             from Philox (tag 5), no dead border. 1 needs
+                             128 x 128 tiles and L >= 256. The work-group layer
+                             (single-hit double tiling) is the same in both.   */
 } kpz_opts;
 
 /* Roughness at the current time (eq. Wdef). Heights are taken in the gauge
@@ -135,7 +143,8 @@ kpz_status kpz_set_slopes(kpz_ctx* ctx, const uint32_t* host_in, int64_t h00, ui
  * job stop and resume). kpz_ckpt_save writes the context's whole state to
  * the file `path` (created or truncated):
  *   header   "KPZCKPT1", version 1, L, p, q (as given to kpz_init), the
- *            thresholds Tp, Tq, seed, sample, tile shape (bx, by), the sweep
+ *            thresholds Tp, Tq, seed, sample, tile shape (bx, by), the device-layer
+ *            decomposition (kpz_opts.decomposition), the sweep
  *            counter t_mcs and the absolute height of site (0,0);
  *   payload  the lattice in the packed exchange format (L*L/16 uint32,
  *            row-major, as kpz_slopes), written in bands;

@@ -26,6 +26,7 @@ struct kpz_ctx {
   uint64_t seed = 0;
   uint32_t run = 1, wpc = 8;
   uint32_t tile_y = 128;               // tile height in sites (128 or 256)
+  uint32_t decomposition = 0;          // device layer: 0 dead border, 1 tile sets
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_buf = false;
@@ -152,6 +153,8 @@ kpz_status kpz_init(kpz_ctx** out, uint32_t L, double p, double q, uint64_t seed
     return KPZ_EINVAL;
   kpz_opts o{};
   if (opts) o = *opts;
+  if (o.decomposition > 1u || (o.decomposition == 1u && ((o.by != 0 && o.by != kTile) || L < 2u * kTile)))
+    return KPZ_EINVAL;
   if ((o.bx != 0 && o.bx != kTile) ||
       (o.by != 0 && o.by != kTile && !(o.by == 2u * kTile && L >= 2u * kTile)))
     return KPZ_EINVAL;
@@ -179,6 +182,7 @@ kpz_status kpz_init(kpz_ctx** out, uint32_t L, double p, double q, uint64_t seed
   ctx->seed = seed;
   ctx->sample = sample;
   ctx->tile_y = o.by ? o.by : kTile;
+  ctx->decomposition = o.decomposition;
   ctx->run = o.run ? o.run : std::min(8u, ntx);   // tiles per work-queue chunk
   ctx->wpc = o.warps_per_cta ? o.warps_per_cta : 8u;
   ctx->stream = (cudaStream_t)o.stream;
@@ -233,7 +237,8 @@ kpz_status kpz_run(kpz_ctx* ctx, uint64_t n_mcs) {
     const uint32_t chunk = (uint32_t)std::min<uint64_t>(n_mcs, 1u << 20);
     for (uint32_t i = 0; i < chunk; ++i) {
       P.s_add = i;
-      KPZ_CUDA(launch_sweep(P, ctx->wpc, ctx->stream));
+      if (ctx->decomposition == 1u) KPZ_CUDA(launch_sweep_tilesets(P, ctx->stream));
+      else                          KPZ_CUDA(launch_sweep(P, ctx->wpc, ctx->stream));
     }
     KPZ_CUDA(launch_advance(ctx->t_dev, chunk, ctx->stream));
     ctx->t_host += chunk;
@@ -336,7 +341,7 @@ struct CkptHeader {
   double p, q;
   uint32_t Tp, Tq;
   uint64_t seed;
-  uint32_t sample, bx, by, reserved;
+  uint32_t sample, bx, by, decomposition;
   uint64_t t_mcs;
   int64_t h00;
 };
@@ -379,6 +384,7 @@ kpz_status kpz_ckpt_save(kpz_ctx* ctx, const char* path) {
   hd.sample = ctx->sample;
   hd.bx = kTile;
   hd.by = ctx->tile_y;
+  hd.decomposition = ctx->decomposition;
   unsigned long long small[2];
   KPZ_CUDA(cudaMemcpyAsync(small, ctx->t_dev, sizeof(small), cudaMemcpyDeviceToHost, ctx->stream));
   KPZ_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -415,13 +421,15 @@ kpz_status kpz_ckpt_load(kpz_ctx** out, const char* path, const kpz_opts* opts) 
   CkptHeader hd{};
   if (fread(&hd, sizeof(hd), 1, in.f) != 1 || memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != 1 ||
       !valid_L(hd.L) || hd.bx != kTile || (hd.by != kTile && hd.by != 2u * kTile) ||
-      acceptance_threshold(hd.p) != hd.Tp || acceptance_threshold(hd.q) != hd.Tq)
+      acceptance_threshold(hd.p) != hd.Tp || acceptance_threshold(hd.q) != hd.Tq || hd.decomposition > 1u)
     return KPZ_ECKPT;
   kpz_opts o{};
   if (opts) o = *opts;
   if ((o.bx != 0 && o.bx != hd.bx) || (o.by != 0 && o.by != hd.by)) return KPZ_EINVAL;
+  if (o.decomposition != 0 && o.decomposition != hd.decomposition) return KPZ_EINVAL;
   o.bx = hd.bx;
   o.by = hd.by;
+  o.decomposition = hd.decomposition;
   kpz_ctx* ctx = nullptr;
   kpz_status st = kpz_init(&ctx, hd.L, hd.p, hd.q, hd.seed, hd.sample, 0, &o);
   if (st) return st;

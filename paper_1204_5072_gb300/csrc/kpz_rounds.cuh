@@ -39,6 +39,10 @@ struct TileCtx {
   uint32_t xo, yo, co, cyo;  // site (0,0): column, row in the cell, cell, cell row
   const uint4* rk;        // round keys in shared memory (kSK)
   uint32_t pm;            // all ones when the tile's site (0,0) is odd (run-time parity)
+  // Tiles without a dead border (kLive, one cell row per lane): bit 0 of
+  // hxl[y'] is the site left of the tile in row y' of the lane's cell row;
+  // hyu[x'] (lane 0) the row above the tile, cells as in T.
+  uint32_t hxl[4], hyu[4];
 };
 
 template <bool kSK>
@@ -86,7 +90,7 @@ __device__ __forceinline__ void acceptance(const SweepParams& P, const TileCtx& 
 // taken at run time from tc.pm (all ones when odd). Xi[r], Yi[r]: position
 // bits of cell row r. Selected sites are never neighbours of each other, so
 // masks taken before any flip equal masks taken site by site.
-template <int QX, int QY, bool kGeneral, int kPar, int CR>
+template <int QX, int QY, bool kGeneral, int kPar, int CR, bool kLive = false>
 __device__ __forceinline__ void quad_masks(const uint32_t (&T)[CR][4][4], const uint32_t (&Xi)[CR],
                                            const uint32_t (&Yi)[CR], const uint32_t (&hx)[CR][4],
                                            const uint32_t (&hy)[4], const TileCtx& tc,
@@ -97,6 +101,7 @@ __device__ __forceinline__ void quad_masks(const uint32_t (&T)[CR][4][4], const 
   if (QY == 0) {
     ysh[0] = __shfl_up_sync(kFull, T[CR - 1][3][x0], 1);
     ysh[1] = __shfl_up_sync(kFull, T[CR - 1][3][x0 + 1], 1);
+    if (kLive && tc.first_row_ok == 0u) { ysh[0] = tc.hyu[x0]; ysh[1] = tc.hyu[x0 + 1]; }
   } else {
     const uint32_t d0 = __shfl_down_sync(kFull, T[0][0][x0], 1);
     const uint32_t d1 = __shfl_down_sync(kFull, T[0][0][x0 + 1], 1);
@@ -110,13 +115,15 @@ __device__ __forceinline__ void quad_masks(const uint32_t (&T)[CR][4][4], const 
     sel[0][1] = Xi[row] & ~Yi[row];
     sel[1][0] = ~Xi[row] & Yi[row];
     sel[1][1] = Xi[row] & Yi[row];
-    if (QX == 0) { sel[0][0] &= ~1u; sel[1][0] &= ~1u; }            // tile column u = 0
-    if (QY == 0 && row == 0) { sel[0][0] &= tc.first_row_ok; sel[0][1] &= tc.first_row_ok; }  // v = 0
+    if (!kLive) {   // dead border: tile column u = 0 and row v = 0
+      if (QX == 0) { sel[0][0] &= ~1u; sel[1][0] &= ~1u; }
+      if (QY == 0 && row == 0) { sel[0][0] &= tc.first_row_ok; sel[0][1] &= tc.first_row_ok; }
+    }
     uint32_t xn[2], yn[2];  // neighbours outside the cell (x) and outside the cell row (y)
 #pragma unroll
     for (int d = 0; d < 2; ++d) {
-      xn[d] = (QX == 0) ? (T[row][y0 + d][3] << 1)                                 // cell c-1, col 3
-                        : __funnelshift_r(T[row][y0 + d][0], hx[row][y0 + d], 1);  // cell c+1, col 0
+      xn[d] = (QX == 0) ? ((T[row][y0 + d][3] << 1) | (kLive ? tc.hxl[y0 + d] : 0u))  // cell c-1, col 3
+                        : __funnelshift_r(T[row][y0 + d][0], hx[row][y0 + d], 1);     // cell c+1, col 0
       if (QY == 0) yn[d] = (row > 0) ? T[row > 0 ? row - 1 : 0][3][x0 + d] : ysh[d];
       else         yn[d] = (row < CR - 1) ? T[row < CR - 1 ? row + 1 : 0][0][x0 + d] : ysh[d];
     }
@@ -169,7 +176,7 @@ __device__ __forceinline__ void quad_flips(uint32_t (&T)[CR][4][4], const uint32
 // takes masks and flips in one branch; the general path takes the masks in
 // one branch, decides acceptance for all quadrants with the same code (one
 // copy of the acceptance draws), then flips in a second branch.
-template <bool kGeneral, int kPar, bool kTrack, int CR, bool kSK>
+template <bool kGeneral, int kPar, bool kTrack, int CR, bool kSK, bool kLive = false>
 __device__ __forceinline__ void one_round(uint32_t (&T)[CR][4][4], const uint32_t (&Xi)[CR],
                                           const uint32_t (&Yi)[CR], const uint32_t (&hx)[CR][4],
                                           const uint32_t (&hy)[4], const SweepParams& P,
@@ -178,22 +185,22 @@ __device__ __forceinline__ void one_round(uint32_t (&T)[CR][4][4], const uint32_
   uint32_t fmin[CR][2][2], fmax[CR][2][2];
   if (!kGeneral) {
     switch (k) {
-      case 0: quad_masks<0, 0, false, kPar, CR>(T, Xi, Yi, hx, hy, tc, fmin, fmax);
+      case 0: quad_masks<0, 0, false, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, fmin, fmax);
               quad_flips<0, 0, kTrack, CR>(T, fmin, fmax, tc, lane, dh); break;
-      case 1: quad_masks<1, 0, false, kPar, CR>(T, Xi, Yi, hx, hy, tc, fmin, fmax);
+      case 1: quad_masks<1, 0, false, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, fmin, fmax);
               quad_flips<1, 0, kTrack, CR>(T, fmin, fmax, tc, lane, dh); break;
-      case 2: quad_masks<0, 1, false, kPar, CR>(T, Xi, Yi, hx, hy, tc, fmin, fmax);
+      case 2: quad_masks<0, 1, false, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, fmin, fmax);
               quad_flips<0, 1, kTrack, CR>(T, fmin, fmax, tc, lane, dh); break;
-      default: quad_masks<1, 1, false, kPar, CR>(T, Xi, Yi, hx, hy, tc, fmin, fmax);
+      default: quad_masks<1, 1, false, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, fmin, fmax);
                quad_flips<1, 1, kTrack, CR>(T, fmin, fmax, tc, lane, dh); break;
     }
     return;
   }
   switch (k) {
-    case 0: quad_masks<0, 0, true, kPar, CR>(T, Xi, Yi, hx, hy, tc, fmin, fmax); break;
-    case 1: quad_masks<1, 0, true, kPar, CR>(T, Xi, Yi, hx, hy, tc, fmin, fmax); break;
-    case 2: quad_masks<0, 1, true, kPar, CR>(T, Xi, Yi, hx, hy, tc, fmin, fmax); break;
-    default: quad_masks<1, 1, true, kPar, CR>(T, Xi, Yi, hx, hy, tc, fmin, fmax); break;
+    case 0: quad_masks<0, 0, true, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, fmin, fmax); break;
+    case 1: quad_masks<1, 0, true, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, fmin, fmax); break;
+    case 2: quad_masks<0, 1, true, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, fmin, fmax); break;
+    default: quad_masks<1, 1, true, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, fmin, fmax); break;
   }
 #pragma unroll
   for (int row = 0; row < CR; ++row) {
@@ -216,7 +223,7 @@ __device__ __forceinline__ void one_round(uint32_t (&T)[CR][4][4], const uint32_
 
 // The 16 single-hit rounds of one tile, two rounds per Philox block of
 // positions of each cell row (counter: cell row cy = CR*lane + r, round pair).
-template <bool kGeneral, int kPar, bool kTrack, int CR, bool kSK>
+template <bool kGeneral, int kPar, bool kTrack, int CR, bool kSK, bool kLive = false>
 __device__ __forceinline__ void tile_rounds(uint32_t (&T)[CR][4][4], const uint32_t (&hx)[CR][4],
                                             const uint32_t (&hy)[4], const SweepParams& P,
                                             const TileCtx& tc, uint32_t lane, int& dh) {
@@ -228,8 +235,8 @@ __device__ __forceinline__ void tile_rounds(uint32_t (&T)[CR][4][4], const uint3
       const uint4 pos = draw<kSK>(P, tc, (kTagPos << 28) | ((CR * lane + row) << 3) | rp);
       X0[row] = pos.x; Y0[row] = pos.y; X1[row] = pos.z; Y1[row] = pos.w;
     }
-    one_round<kGeneral, kPar, kTrack, CR, kSK>(T, X0, Y0, hx, hy, P, tc, lane, 2u * rp, dh);
-    one_round<kGeneral, kPar, kTrack, CR, kSK>(T, X1, Y1, hx, hy, P, tc, lane, 2u * rp + 1u, dh);
+    one_round<kGeneral, kPar, kTrack, CR, kSK, kLive>(T, X0, Y0, hx, hy, P, tc, lane, 2u * rp, dh);
+    one_round<kGeneral, kPar, kTrack, CR, kSK, kLive>(T, X1, Y1, hx, hy, P, tc, lane, 2u * rp + 1u, dh);
   }
 }
 

@@ -25,10 +25,10 @@ def eng():
     return engine()
 
 
-def _ensemble(eng, L, p, q, ts, n, seed=1):
+def _ensemble(eng, L, p, q, ts, n, seed=1, decomposition=0):
     W = np.zeros((n, len(ts)))
     for k in range(n):
-        lat = eng.Lattice(L, p, q, seed=seed, sample=k)
+        lat = eng.Lattice(L, p, q, seed=seed, sample=k, decomposition=decomposition)
         t0 = 0
         for j, t in enumerate(ts):
             if t > t0:
@@ -74,3 +74,31 @@ def test_edwards_wilkinson_grows_slower(eng):
     kpz = _ensemble(eng, 256, 1.0, 0.0, ts, 4).mean(0)
     ew = _ensemble(eng, 256, 0.5, 0.5, ts, 4).mean(0)
     assert ew[1] / ew[0] < 0.6 * kpz[1] / kpz[0]
+
+
+def test_both_device_layers_against_random_sequential_updates(eng):
+    """Dead-border tiles (the paper's KPZ scheme) and the tile-set double
+    tiling (no dead border) at L = 256 against random-sequential updates:
+    both stay within the early-time offset of the single-hit work-group
+    layer and grow with the same exponent; the two device layers agree with
+    each other within errors (the offset comes from the work-group layer)."""
+    L, ts, n = 256, [1, 2, 4, 8, 16, 32, 64], 16
+    rsu = np.zeros((n, len(ts)))
+    for k in range(n):
+        st = O.State.flat(L)
+        for j, t in enumerate(ts):
+            st.rsu(t - st.t, 1.0, 0.0, seed=12, sample=k)
+            rsu[k, j] = st.w2()
+    mr = rsu.mean(0)
+    means = {}
+    for dec in (0, 1):
+        W = _ensemble(eng, L, 1.0, 0.0, ts, 48, seed=21 + dec, decomposition=dec)
+        mg = W.mean(0)
+        means[dec] = (mg, W.var(0, ddof=1) / W.shape[0])
+        rel = mg / mr - 1
+        assert np.all(np.abs(rel) < 0.07), (dec, rel)
+        bg = np.polyfit(np.log(ts[3:]), np.log(mg[3:]), 1)[0] / 2
+        br = np.polyfit(np.log(ts[3:]), np.log(mr[3:]), 1)[0] / 2
+        assert abs(bg - br) < 0.04, (dec, bg, br)
+    (m0, v0), (m1, v1) = means[0], means[1]
+    assert np.all(np.abs(m0 - m1) < 0.02 * m0 + 4 * np.sqrt(v0 + v1)), (m0, m1)
