@@ -41,6 +41,7 @@
  *     level n uses bit b of A_{n>>2}[n&3];  U = sum_n bit << (15-n)
  *   a minimum flips iff U < Tp, a maximum flips iff U < Tq,
  *   Tp = min(65536, floor(p*65536 + 0.5)), likewise Tq.
+ * C = 2 variant (orc_sweep_c2): 2 x 2 cells, 4 rounds, no position draw.
  * Tile-set variant (orc_sweep_tilesets): same origin and tiles, no dead border,
  * the four sets (tx & 1) + 2 (ty & 1) swept in an order drawn from
  * philox(5<<28, 0, s, sample) (orc_tileset_order).
@@ -295,6 +296,68 @@ int orc_sweep(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32_t Tq,
     for (uint32_t n = 0; n < ntiles; ++n) {
         uint32_t T = tile_order[n];
         tile_rounds(&P, s, T, ox, oy, rounds, order, cell_order, &mpos, macc, sx, sy, NULL, h00);
+    }
+    free(tile_order);
+    free(cell_order);
+    return 0;
+}
+
+/* The C = 2 limit of the work-group layer (cells of 2 x 2 sites, their four
+ * 1 x 1 quadrants as the sets, 4 single-hit rounds per sweep): in round r of
+ * tile T the set k = (philox(1<<28, T, s, sample).w0 >> 2r) & 3 is active, and
+ * every 2 x 2 cell (cx, cy) attempts its site u = 2cx + (k & 1),
+ * v = 2cy + (k >> 1) (no position draw; dead if u == 0 or v == 0). The
+ * acceptance number of that attempt (16 bits, level 0 most significant):
+ *   with 4 x 4 storage cell (c4x, c4y) = (u >> 2, v >> 2), site index inside
+ *   it a = 2 ((v >> 1) & 1) + ((u >> 1) & 1), word wx = c4x >> 5,
+ *   nwx = ceil(Bx/128): A_m = philox(3<<28 | ((c4y*nwx+wx) << 6) | (r << 4)
+ *   | (a << 2) | m, T, s, sample), level n from bit (c4x & 31) of
+ *   A_{n>>2}[n&3]. Returns 0, or -1 on bad input. */
+int orc_sweep_c2(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32_t Tq,
+                 uint64_t seed, uint32_t sample, uint32_t s,
+                 uint8_t* sx, uint8_t* sy, int64_t* h00, uint64_t order) {
+    if (L < 4 || (L & (L - 1)) || Bx < 4 || By < 4 || (Bx & (Bx - 1)) || (By & (By - 1)) ||
+        Bx > L || By > L || Tp > 65536u || Tq > 65536u)
+        return -1;
+    uint32_t w[4];
+    philox_at((uint32_t)TAG_ORIGIN << 28, 0, s, sample, seed, w);
+    uint32_t ox = w[0] & (L - 1), oy = w[1] & (L - 1);
+    uint32_t ntx = L / Bx, nty = L / By, ntiles = ntx * nty;
+    uint32_t ncx = Bx / 2, ncy = By / 2, ncells = ncx * ncy, nwx = words_per_cell_row(Bx);
+    uint32_t* tile_order = (uint32_t*)malloc(sizeof(uint32_t) * ntiles);
+    uint32_t* cell_order = (uint32_t*)malloc(sizeof(uint32_t) * ncells);
+    if (!tile_order || !cell_order) { free(tile_order); free(cell_order); return -1; }
+    shuffle(tile_order, ntiles, order >= 2 ? order : 0);
+    if (order == 1)
+        for (uint32_t n = 0; n < ntiles; ++n) tile_order[n] = ntiles - 1 - n;
+    memo macc[4] = {{0}};
+    for (uint32_t n = 0; n < ntiles; ++n) {
+        uint32_t T = tile_order[n], tx = T % ntx, ty = T / ntx;
+        uint32_t x0 = ox + tx * Bx, y0 = oy + ty * By;
+        uint32_t setw[4];
+        philox_at((uint32_t)TAG_SET << 28, T, s, sample, seed, setw);
+        for (uint32_t r = 0; r < 4; ++r) {
+            uint32_t k = (setw[0] >> (2 * r)) & 3u;
+            shuffle(cell_order, ncells, order >= 2 ? order * 0x9E3779B97F4A7C15ull + T + 1 : 0);
+            if (order == 1)
+                for (uint32_t c = 0; c < ncells; ++c) cell_order[c] = ncells - 1 - c;
+            for (uint32_t c = 0; c < ncells; ++c) {
+                uint32_t cell = cell_order[c];
+                uint32_t u = 2 * (cell % ncx) + (k & 1u), v = 2 * (cell / ncx) + (k >> 1);
+                if (u == 0 || v == 0) continue;          /* dead border of the tile */
+                uint32_t c4x = u >> 2, c4y = v >> 2, a = 2 * ((v >> 1) & 1u) + ((u >> 1) & 1u);
+                uint32_t row_word = c4y * nwx + (c4x >> 5), b = c4x & 31u, U = 0;
+                for (uint32_t lev = 0; lev < 16; ++lev) {
+                    uint32_t mi = lev >> 2;
+                    uint32_t idx = ((uint32_t)TAG_ACC << 28) | (row_word << 6) | (r << 4) | (a << 2) | mi;
+                    const uint32_t* aw = memo_philox(&macc[mi], idx, T, s, sample, seed);
+                    U |= ((aw[lev & 3u] >> b) & 1u) << (15 - lev);
+                }
+                uint32_t i = (x0 + u) & (L - 1), j = (y0 + v) & (L - 1);
+                int dh = orc_attempt(L, sx, sy, i, j, U < Tp, U < Tq);
+                if (dh != 0 && i == 0 && j == 0 && h00) *h00 += dh;
+            }
+        }
     }
     free(tile_order);
     free(cell_order);

@@ -87,6 +87,10 @@ def lib():
             L.orc_sweep_tilesets.restype = c.c_int
             L.orc_tileset_order.argtypes = [c.c_uint32, c.c_uint32, c.c_uint64, u32p]
             L.orc_tileset_order.restype = c.c_int
+            L.orc_sweep_c2.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32,
+                                       c.c_uint64, c.c_uint32, c.c_uint32, u8p, u8p,
+                                       c.POINTER(c.c_int64), c.c_uint64]
+            L.orc_sweep_c2.restype = c.c_int
             _lib = L
     return _lib
 
@@ -168,6 +172,22 @@ class State:
             raise ValueError("invalid oracle parameters")
         self.h00 = h.value
         self.t += 1
+        return self
+
+    def sweep_c2(self, Bx, By, p, q, seed, sample=0, order=0):
+        """One sweep with the C = 2 work-group layer (2 x 2 cells, 4 rounds)."""
+        h = ctypes.c_int64(self.h00)
+        rc = lib().orc_sweep_c2(self.L, Bx, By, threshold(p), threshold(q), seed, sample, self.t,
+                                self.sx, self.sy, ctypes.byref(h), order)
+        if rc:
+            raise ValueError("invalid oracle parameters")
+        self.h00 = h.value
+        self.t += 1
+        return self
+
+    def run_c2(self, n, Bx, By, p, q, seed, sample=0):
+        for _ in range(n):
+            self.sweep_c2(Bx, By, p, q, seed, sample)
         return self
 
     def run_tilesets(self, n, Bx, By, p, q, seed, sample=0):
