@@ -82,6 +82,12 @@ typedef struct {
                              from Philox (tag 5), no dead border. 1 needs
                              128 x 128 tiles and L >= 256. The work-group layer
                              (single-hit double tiling) is the same in both.   */
+    uint32_t cell;        /* work-group layer cell edge (Sec. 3.1): 4 (0 = 4):
+                             4 x 4 cells, 2 x 2 quadrant sets, 16 rounds per
+                             sweep; or 2: the C = 2 limit, 2 x 2 cells whose
+                             1 x 1 quadrants are the sets, 4 rounds per sweep,
+                             no position draw (needs 128 x 128 tiles and
+                             decomposition 0)                                  */
 } kpz_opts;
 
 /* Roughness at the current time (eq. Wdef). Heights are taken in the gauge
@@ -144,7 +150,7 @@ kpz_status kpz_set_slopes(kpz_ctx* ctx, const uint32_t* host_in, int64_t h00, ui
  * the file `path` (created or truncated):
  *   header   "KPZCKPT1", version 1, L, p, q (as given to kpz_init), the
  *            thresholds Tp, Tq, seed, sample, tile shape (bx, by), the device-layer
- *            decomposition (kpz_opts.decomposition), the sweep
+ *            decomposition and cell edge (kpz_opts.decomposition, .cell), the sweep
  *            counter t_mcs and the absolute height of site (0,0);
  *   payload  the lattice in the packed exchange format (L*L/16 uint32,
  *            row-major, as kpz_slopes), written in bands;

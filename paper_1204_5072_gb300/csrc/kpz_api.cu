@@ -27,6 +27,7 @@ struct kpz_ctx {
   uint32_t run = 1, wpc = 8;
   uint32_t tile_y = 128;               // tile height in sites (128 or 256)
   uint32_t decomposition = 0;          // device layer: 0 dead border, 1 tile sets
+  uint32_t cell = 4;                   // work-group cell edge: 4 or 2
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_buf = false;
@@ -115,6 +116,7 @@ SweepParams sweep_params(const kpz_ctx* c) {
   P.sample = c->sample;
   P.h00 = c->h00;
   P.queue = c->queue;
+  P.cell = c->cell;
   return P;
 }
 
@@ -155,6 +157,9 @@ kpz_status kpz_init(kpz_ctx** out, uint32_t L, double p, double q, uint64_t seed
   if (opts) o = *opts;
   if (o.decomposition > 1u || (o.decomposition == 1u && ((o.by != 0 && o.by != kTile) || L < 2u * kTile)))
     return KPZ_EINVAL;
+  if ((o.cell != 0 && o.cell != 4u && o.cell != 2u) ||
+      (o.cell == 2u && (o.decomposition != 0u || (o.by != 0 && o.by != kTile))))
+    return KPZ_EINVAL;
   if ((o.bx != 0 && o.bx != kTile) ||
       (o.by != 0 && o.by != kTile && !(o.by == 2u * kTile && L >= 2u * kTile)))
     return KPZ_EINVAL;
@@ -183,6 +188,7 @@ kpz_status kpz_init(kpz_ctx** out, uint32_t L, double p, double q, uint64_t seed
   ctx->sample = sample;
   ctx->tile_y = o.by ? o.by : kTile;
   ctx->decomposition = o.decomposition;
+  ctx->cell = o.cell ? o.cell : 4u;
   ctx->run = o.run ? o.run : std::min(8u, ntx);   // tiles per work-queue chunk
   ctx->wpc = o.warps_per_cta ? o.warps_per_cta : 8u;
   ctx->stream = (cudaStream_t)o.stream;
@@ -384,7 +390,7 @@ kpz_status kpz_ckpt_save(kpz_ctx* ctx, const char* path) {
   hd.sample = ctx->sample;
   hd.bx = kTile;
   hd.by = ctx->tile_y;
-  hd.decomposition = ctx->decomposition;
+  hd.decomposition = ctx->decomposition | (ctx->cell == 2u ? 0x100u : 0u);   // bit 8: C = 2
   unsigned long long small[2];
   KPZ_CUDA(cudaMemcpyAsync(small, ctx->t_dev, sizeof(small), cudaMemcpyDeviceToHost, ctx->stream));
   KPZ_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -421,15 +427,17 @@ kpz_status kpz_ckpt_load(kpz_ctx** out, const char* path, const kpz_opts* opts) 
   CkptHeader hd{};
   if (fread(&hd, sizeof(hd), 1, in.f) != 1 || memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != 1 ||
       !valid_L(hd.L) || hd.bx != kTile || (hd.by != kTile && hd.by != 2u * kTile) ||
-      acceptance_threshold(hd.p) != hd.Tp || acceptance_threshold(hd.q) != hd.Tq || hd.decomposition > 1u)
+      acceptance_threshold(hd.p) != hd.Tp || acceptance_threshold(hd.q) != hd.Tq || (hd.decomposition & ~0x100u) > 1u)
     return KPZ_ECKPT;
   kpz_opts o{};
   if (opts) o = *opts;
   if ((o.bx != 0 && o.bx != hd.bx) || (o.by != 0 && o.by != hd.by)) return KPZ_EINVAL;
-  if (o.decomposition != 0 && o.decomposition != hd.decomposition) return KPZ_EINVAL;
+  const uint32_t dec = hd.decomposition & 0xFFu, cell = (hd.decomposition & 0x100u) ? 2u : 4u;
+  if ((o.decomposition != 0 && o.decomposition != dec) || (o.cell != 0 && o.cell != cell)) return KPZ_EINVAL;
   o.bx = hd.bx;
   o.by = hd.by;
-  o.decomposition = hd.decomposition;
+  o.decomposition = dec;
+  o.cell = cell;
   kpz_ctx* ctx = nullptr;
   kpz_status st = kpz_init(&ctx, hd.L, hd.p, hd.q, hd.seed, hd.sample, 0, &o);
   if (st) return st;

@@ -42,6 +42,7 @@ struct SweepParams {
   uint32_t sample;          // realisation index (Philox counter word 3)
   unsigned long long* h00;  // absolute height of site (0,0), two's complement
   uint32_t* queue;          // single-lattice sweep: work-queue counter, 0 between launches
+  uint32_t cell;            // work-group cell edge: 4 (default) or 2 (the C = 2 limit)
 };
 
 cudaError_t launch_sweep(const SweepParams& P, uint32_t warps_per_cta, cudaStream_t st);

@@ -51,23 +51,22 @@ __device__ __forceinline__ uint4 draw(const SweepParams& P, const TileCtx& tc, u
   return philox(c0, tc.tid, tc.s, P.sample, P.k0, P.k1);
 }
 
-// Bit-serial comparison U < T for the 32 cells of cell row cy (U uniform
+// Bit-serial comparison U < T for the 32 cells of a cell row (U uniform
 // 16-bit, level n = bit 15-n of U taken from bit c of word n&3 of Philox call
-// n>>2). Only cells in needp (selected site is a minimum) and needq (a
+// n>>2, call m at counter word 0 = tag 3 << 28 | base | m). Only cells in needp (selected site is a minimum) and needq (a
 // maximum) need a decision; a cell is decided at the first level where U and
 // T differ, so the warp stops drawing levels once no cell of any lane is still
 // tied. The outcome equals the full 16-level comparison.
 template <bool kSK>
-__device__ __forceinline__ void acceptance(const SweepParams& P, const TileCtx& tc, uint32_t cy,
-                                           uint32_t r, uint32_t needp, uint32_t needq,
-                                           uint32_t& AP, uint32_t& AQ) {
+__device__ __forceinline__ void acceptance(const SweepParams& P, const TileCtx& tc, uint32_t base,
+                                           uint32_t needp, uint32_t needq, uint32_t& AP, uint32_t& AQ) {
   uint32_t ltp = 0u, ltq = 0u;
   uint32_t undp = (P.Tp == 0u || (P.Tp >> 16)) ? 0u : needp;
   uint32_t undq = (P.Tq == 0u || (P.Tq >> 16)) ? 0u : needq;
 #pragma unroll 1
   for (uint32_t m = 0; m < 4; ++m) {
     if (4u * m >= P.nlev || !__any_sync(0xffffffffu, (undp | undq) != 0u)) break;
-    const uint4 A = draw<kSK>(P, tc, (kTagAcc << 28) | (cy << 6) | (r << 2) | m);
+    const uint4 A = draw<kSK>(P, tc, (kTagAcc << 28) | base | m);
     const uint32_t w[4] = {A.x, A.y, A.z, A.w};
 #pragma unroll
     for (uint32_t j = 0; j < 4; ++j) {
@@ -205,7 +204,7 @@ __device__ __forceinline__ void one_round(uint32_t (&T)[CR][4][4], const uint32_
 #pragma unroll
   for (int row = 0; row < CR; ++row) {
     uint32_t AP, AQ;
-    acceptance<kSK>(P, tc, CR * lane + row, r,
+    acceptance<kSK>(P, tc, ((CR * lane + row) << 6) | (r << 2),
                     fmin[row][0][0] | fmin[row][0][1] | fmin[row][1][0] | fmin[row][1][1],
                     fmax[row][0][0] | fmax[row][0][1] | fmax[row][1][0] | fmax[row][1][1], AP, AQ);
 #pragma unroll
@@ -237,6 +236,84 @@ __device__ __forceinline__ void tile_rounds(uint32_t (&T)[CR][4][4], const uint3
     }
     one_round<kGeneral, kPar, kTrack, CR, kSK, kLive>(T, X0, Y0, hx, hy, P, tc, lane, 2u * rp, dh);
     one_round<kGeneral, kPar, kTrack, CR, kSK, kLive>(T, X1, Y1, hx, hy, P, tc, lane, 2u * rp + 1u, dh);
+  }
+}
+
+// The C = 2 limit of the work-group layer (one cell row per lane): 2 x 2
+// cells whose four 1 x 1 quadrants are the sets. In a round with set (QX, QY)
+// every 2 x 2 cell attempts its site (QX, QY), i.e. the four sites
+// (QX + 2i, QY + 2j) of every 4 x 4 storage cell, no two of them neighbours.
+// No position draws; the acceptance numbers of site a = 2j + i of the storage
+// cells of cell row `lane` in round r use counter base lane << 6 | r << 4 | a << 2.
+template <int QX, int QY, bool kGeneral, int kPar, bool kTrack, bool kSK>
+__device__ __forceinline__ void c2_round(uint32_t (&T)[4][4], const uint32_t (&hx)[4],
+                                         const uint32_t (&hy)[4], const SweepParams& P,
+                                         const TileCtx& tc, uint32_t lane, uint32_t r, int& dh) {
+  uint32_t ysh[2];   // neighbour in another lane of column QX + 2i
+  if (QY == 0) {
+    ysh[0] = __shfl_up_sync(kFull, T[3][QX], 1);
+    ysh[1] = __shfl_up_sync(kFull, T[3][QX + 2], 1);
+  } else {
+    const uint32_t d0 = __shfl_down_sync(kFull, T[0][QX], 1);
+    const uint32_t d1 = __shfl_down_sync(kFull, T[0][QX + 2], 1);
+    ysh[0] = tc.last_lane ? hy[QX] : d0;
+    ysh[1] = tc.last_lane ? hy[QX + 2] : d1;
+  }
+  uint32_t fmin[2][2], fmax[2][2];   // [j][i]: site (QX + 2i, QY + 2j)
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int xp = QX + 2 * i, yp = QY + 2 * j;
+      const uint32_t s = T[yp][xp];
+      const uint32_t nL = (xp > 0) ? T[yp][xp > 0 ? xp - 1 : 0] : (T[yp][3] << 1);
+      const uint32_t nR = (xp < 3) ? T[yp][xp < 3 ? xp + 1 : 3] : __funnelshift_r(T[yp][0], hx[yp], 1);
+      const uint32_t nU = (yp > 0) ? T[yp > 0 ? yp - 1 : 0][xp] : ysh[i];
+      const uint32_t nD = (yp < 3) ? T[yp < 3 ? yp + 1 : 3][xp] : ysh[i];
+      uint32_t sel = ~0u;
+      if (xp == 0) sel &= ~1u;                 // tile column u = 0
+      if (yp == 0) sel &= tc.first_row_ok;     // tile row v = 0
+      const uint32_t v = ((kPar + xp + yp) & 1) ? ~s : s;   // bit of a higher neighbour
+      const uint32_t hL = ~(nL ^ v), hR = ~(nR ^ v), hU = ~(nU ^ v), hD = ~(nD ^ v);
+      fmin[j][i] = sel & hL & hR & hU & hD;
+      fmax[j][i] = kGeneral ? (sel & ~hL & ~hR & ~hU & ~hD) : 0u;
+    }
+  if (kGeneral) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        uint32_t AP, AQ;
+        acceptance<kSK>(P, tc, (lane << 6) | (r << 4) | (uint32_t)((2 * j + i) << 2), fmin[j][i],
+                        fmax[j][i], AP, AQ);
+        fmin[j][i] &= AP;
+        fmax[j][i] &= AQ;
+      }
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int xp = QX + 2 * i, yp = QY + 2 * j;
+      if (kTrack && lane == tc.cyo && (uint32_t)xp == tc.xo && (uint32_t)yp == tc.yo)
+        dh += 2 * (int)((fmin[j][i] >> tc.co) & 1u) - 2 * (int)((fmax[j][i] >> tc.co) & 1u);
+      T[yp][xp] ^= fmin[j][i] | fmax[j][i];
+    }
+}
+
+// The four C = 2 rounds of one tile (sets from tc.setw, two bits per round).
+template <bool kGeneral, int kPar, bool kTrack, bool kSK>
+__device__ __forceinline__ void tile_rounds_c2(uint32_t (&T)[4][4], const uint32_t (&hx)[4],
+                                               const uint32_t (&hy)[4], const SweepParams& P,
+                                               const TileCtx& tc, uint32_t lane, int& dh) {
+#pragma unroll 1
+  for (uint32_t r = 0; r < 4u; ++r) {
+    switch ((tc.setw >> (2u * r)) & 3u) {
+      case 0: c2_round<0, 0, kGeneral, kPar, kTrack, kSK>(T, hx, hy, P, tc, lane, r, dh); break;
+      case 1: c2_round<1, 0, kGeneral, kPar, kTrack, kSK>(T, hx, hy, P, tc, lane, r, dh); break;
+      case 2: c2_round<0, 1, kGeneral, kPar, kTrack, kSK>(T, hx, hy, P, tc, lane, r, dh); break;
+      default: c2_round<1, 1, kGeneral, kPar, kTrack, kSK>(T, hx, hy, P, tc, lane, r, dh); break;
+    }
   }
 }
 

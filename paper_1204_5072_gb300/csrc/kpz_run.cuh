@@ -74,12 +74,13 @@ struct WarpStage {
 constexpr uint32_t kMaxWarpsPerCta = 8;
 
 // One run: tiles tx0 .. tx0 + n - 1 of tile row ty (n <= ntx), left to right.
-template <bool kGeneral, int CR, bool kSK, bool kRtPar = false>
+template <bool kGeneral, int CR, bool kSK, bool kRtPar = false, bool kC2 = false>
 __device__ __forceinline__ void sweep_run(const SweepParams& P, WarpStage<CR>& ws, const uint4* rk,
                                           uint32_t lane,
                                           uint32_t s, uint32_t ox, uint32_t oy, uint32_t ty,
                                           uint32_t tx0, uint32_t n) {
   constexpr uint32_t kTileY = kTile * CR;
+  static_assert(!kC2 || CR == 1, "the C = 2 work-group layer holds one cell row per lane");
   const uint32_t L = P.g.L, NR = P.g.NR, NB = P.g.NB;
   // Rows: tile row y' of this lane's cell row r lives in storage cell row
   // Rb + CR lane + r (+1 past a plane wrap), plane row (by+y')%4.
@@ -206,7 +207,16 @@ __device__ __forceinline__ void sweep_run(const SweepParams& P, WarpStage<CR>& w
 
     int dh = 0;
     // The one tile per sweep that holds site (0,0) also counts its moves.
-    if (kRtPar) {   // one copy of the rounds for both parities (tc.pm)
+    if (kC2) {      // C = 2 work-group layer (one cell row per lane)
+      auto& T0 = reinterpret_cast<uint32_t(&)[4][4]>(T[0]);
+      if (tc.track) {
+        if (par) rounds::tile_rounds_c2<kGeneral, 1, true, kSK>(T0, hx[0], hy, P, tc, lane, dh);
+        else     rounds::tile_rounds_c2<kGeneral, 0, true, kSK>(T0, hx[0], hy, P, tc, lane, dh);
+      } else {
+        if (par) rounds::tile_rounds_c2<kGeneral, 1, false, kSK>(T0, hx[0], hy, P, tc, lane, dh);
+        else     rounds::tile_rounds_c2<kGeneral, 0, false, kSK>(T0, hx[0], hy, P, tc, lane, dh);
+      }
+    } else if (kRtPar) {   // one copy of the rounds for both parities (tc.pm)
       if (tc.track) tile_rounds<kGeneral, 2, true, CR, kSK>(T, hx, hy, P, tc, lane, dh);
       else          tile_rounds<kGeneral, 2, false, CR, kSK>(T, hx, hy, P, tc, lane, dh);
     } else if (tc.track) {

@@ -23,7 +23,7 @@ using run::kMaxWarpsPerCta;
 // Every warp makes exactly one fetch past the last chunk; the warp whose
 // fetch is the last of all (nchunks + W - 1) returns the counter to zero for
 // the next launch.
-template <bool kGeneral, int CR>
+template <bool kGeneral, int CR, bool kC2>
 __global__ void __launch_bounds__(256, CR == 1 ? (kGeneral ? 2 : 3) : (kGeneral ? 1 : 2))
 sweep_kernel(const SweepParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -51,14 +51,15 @@ sweep_kernel(const SweepParams P) {
     uint32_t next = 0;
     if (lane == 0) next = atomicAdd(P.queue, 1u);
     const uint32_t ty = c / cpr;
-    run::sweep_run<kGeneral, CR, !kGeneral>(P, ws, rk, lane, s, ox, oy, ty, (c - ty * cpr) * P.run, P.run);
+    run::sweep_run<kGeneral, CR, !kGeneral, false, kC2>(P, ws, rk, lane, s, ox, oy, ty, (c - ty * cpr) * P.run,
+                                                       P.run);
     c = __shfl_sync(kFull, next, 0);
   }
   if (lane == 0 && c == nchunks + W - 1u) atomicExch(P.queue, 0u);
 }
 
 // Resident CTAs per SM of one sweep kernel at wpc warps per CTA (cached per device).
-template <bool kGeneral, int CR>
+template <bool kGeneral, int CR, bool kC2>
 cudaError_t resident_ctas(uint32_t wpc, uint32_t& ctas) {
   constexpr int kMaxDev = 64;
   static std::mutex mu;
@@ -69,10 +70,10 @@ cudaError_t resident_ctas(uint32_t wpc, uint32_t& ctas) {
   std::lock_guard<std::mutex> lock(mu);
   if (dev < kMaxDev && cache[dev][wpc]) { ctas = cache[dev][wpc]; return cudaSuccess; }
   const int bytes = (int)(kMaxWarpsPerCta * sizeof(WarpStage<CR>));
-  e = cudaFuncSetAttribute(sweep_kernel<kGeneral, CR>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  e = cudaFuncSetAttribute(sweep_kernel<kGeneral, CR, kC2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
   int per_sm = 0, sms = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<kGeneral, CR>, (int)(wpc * 32u),
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<kGeneral, CR, kC2>, (int)(wpc * 32u),
                                                     wpc * sizeof(WarpStage<CR>));
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
@@ -81,15 +82,15 @@ cudaError_t resident_ctas(uint32_t wpc, uint32_t& ctas) {
   return cudaSuccess;
 }
 
-template <bool kGeneral, int CR>
+template <bool kGeneral, int CR, bool kC2 = false>
 cudaError_t launch_cr(const SweepParams& P, uint32_t wpc, cudaStream_t st) {
   uint32_t ctas = 0;
-  cudaError_t e = resident_ctas<kGeneral, CR>(wpc, ctas);
+  cudaError_t e = resident_ctas<kGeneral, CR, kC2>(wpc, ctas);
   if (e != cudaSuccess) return e;
   // One wave of resident warps, fewer if there are fewer tiles than warps.
   const uint64_t tiles = (uint64_t)P.ntx * P.nty;
   const uint64_t blocks = std::min<uint64_t>(ctas, (tiles + wpc - 1) / wpc);
-  sweep_kernel<kGeneral, CR><<<(unsigned)blocks, wpc * 32u, wpc * sizeof(WarpStage<CR>), st>>>(P);
+  sweep_kernel<kGeneral, CR, kC2><<<(unsigned)blocks, wpc * 32u, wpc * sizeof(WarpStage<CR>), st>>>(P);
   return cudaSuccess;
 }
 
@@ -104,7 +105,11 @@ cudaError_t launch_sweep(const SweepParams& P, uint32_t warps_per_cta, cudaStrea
   const uint32_t tile_y = P.g.L / P.nty;
   cudaError_t e;
   const bool general = !(P.Tp == 65536u && P.Tq == 0u);
-  if (tile_y == kTile)
+  if (P.cell == 2u && tile_y == kTile)
+    e = general ? launch_cr<true, 1, true>(P, wpc, st) : launch_cr<false, 1, true>(P, wpc, st);
+  else if (P.cell == 2u)
+    return cudaErrorInvalidValue;
+  else if (tile_y == kTile)
     e = general ? launch_cr<true, 1>(P, wpc, st) : launch_cr<false, 1>(P, wpc, st);
   else if (tile_y == 2u * kTile)
     e = general ? launch_cr<true, 2>(P, wpc, st) : launch_cr<false, 2>(P, wpc, st);
