@@ -201,9 +201,10 @@ typedef struct {
     uint32_t n_samples;    /* log-spaced W^2 times up to the longest run (0 = 64);
                               every realisation is also sampled at its own end    */
     int autotune;          /* != 0: time a short probe of the ensemble for every
-                              (tiles per run, warps per block) and keep the fastest
-                              (that choice never changes the results); with
-                              tile_y = 0 also choose the tile height              */
+                              (tiles per run, warps per block), then for fewer
+                              resident blocks per SM, and keep the fastest (these
+                              choices never change the results); with tile_y = 0
+                              also choose the tile height                        */
     uint32_t run;          /* tiles per run when not tuning (power of two, 0 = 4)  */
     uint32_t warps_per_cta;/* 1..8 (0 = 8)                                         */
     uint32_t ctas_per_sm;  /* resident blocks per SM (0 = as many as fit)          */

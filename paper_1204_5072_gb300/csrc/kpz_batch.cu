@@ -617,6 +617,23 @@ kpz_status kpz_batch_create(kpz_batch** out, const kpz_spec* specs, uint32_t n, 
     b->cr = best_cr;
     b->run_max = best_run;
     b->wpc = best_wpc;
+    // Blocks per SM: fewer resident blocks than fit, at the chosen settings.
+    int maxb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxb, kernel_of(b->cr), (int)(b->wpc * 32),
+                                                      smem_bytes(b->wpc, b->cr)) != cudaSuccess)
+      return fail_free(b, KPZ_ECUDA);
+    uint32_t best_cps = 0;
+    for (uint32_t cps = 1; cps < (uint32_t)maxb; ++cps) {
+      b->ctas_per_sm = cps;
+      st = prepare(b, &cap);
+      if (st) return fail_free(b, st);
+      float ms = 0.f;
+      st = run_once(b, &ms);
+      if (st) return fail_free(b, st);
+      if (b->nprobe < 64) b->probe_ms[b->nprobe++] = ms;
+      if (ms < best) { best = ms; best_cps = cps; }
+    }
+    b->ctas_per_sm = best_cps;
   }
   st = prepare(b, nullptr);
   if (st) return fail_free(b, st);
