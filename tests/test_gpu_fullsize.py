@@ -123,3 +123,36 @@ def test_L65536_first_sweep_sampled_tiles_match_oracle(eng, p, q, ty):
         if T == t00:
             dh00 = d
     assert r["h00"] == dh00 and r["t"] == 1
+
+
+@pytest.mark.parametrize("w", ["L4096_P1", "L4096_P095"])
+def test_L4096_ten_thousand_sweeps(eng, w):
+    """The L = 4096, 10^4-sweep workloads (p = 1 and p = 0.95): the first sweep's
+    sampled tiles against the oracle's window computation, then the full run
+    through the W^2 sampling times: a valid surface, the width recomputed on
+    the host, a rerun identical, and W^2 growing as the surface roughens."""
+    from synth import inputs as I
+    W = getattr(I, w)
+    L, Bx = W.L, W.bx
+    lat = eng.Lattice(L, W.p, W.q, seed=W.seed, sample=W.sample)
+    lat.run(1)
+    words = lat.slopes()
+    for T in (0, 31, 17 * 32 + 5, 32 * 32 - 1, 500):
+        sx, sy, (x0, y0), _ = O.flat_tile_sweep(L, Bx, W.by, W.p, W.q, W.seed, W.sample, 0, T)
+        gx, gy = _window(words, L, x0, y0, Bx, W.by)
+        assert np.array_equal(gx, sx) and np.array_equal(gy, sy), (w, T)
+    w2 = []
+    t0 = 1
+    for t in I.sample_times(W.mcs)[1:]:
+        if t > t0:
+            lat.run(t - t0)
+            t0 = t
+        w2.append(lat.roughness()["w2"])
+    r = lat.roughness()
+    words = lat.slopes()
+    _row_col_sums_ok(words, L)
+    assert (r["S1"], r["S2"]) == _w2_host(words, L)
+    assert r["t"] == W.mcs
+    again = eng.Lattice(L, W.p, W.q, seed=W.seed, sample=W.sample).run(W.mcs)
+    assert np.array_equal(again.slopes(), words) and again.roughness()["h00"] == r["h00"]
+    assert w2[-1] > 4 * w2[0] and all(np.isfinite(w2))
