@@ -42,6 +42,7 @@
  *   a minimum flips iff U < Tp, a maximum flips iff U < Tq,
  *   Tp = min(65536, floor(p*65536 + 0.5)), likewise Tq.
  * C = 2 variant (orc_sweep_c2): 2 x 2 cells, 4 rounds, no position draw.
+ * Colour-class random-sequential reference (orc_sweep_colour): tags 6 and 7.
  * Tile-set variant (orc_sweep_tilesets): same origin and tiles, no dead border,
  * the four sets (tx & 1) + 2 (ty & 1) swept in an order drawn from
  * philox(5<<28, 0, s, sample) (orc_tileset_order).
@@ -92,7 +93,8 @@ static void philox_at(uint32_t tag_index, uint32_t c1, uint32_t s, uint32_t samp
     orc_philox(ctr, key, out);
 }
 
-enum { TAG_ORIGIN = 0, TAG_SET = 1, TAG_POS = 2, TAG_ACC = 3, TAG_RSU = 4, TAG_PHASE = 5 };
+enum { TAG_ORIGIN = 0, TAG_SET = 1, TAG_POS = 2, TAG_ACC = 3, TAG_RSU = 4, TAG_PHASE = 5,
+       TAG_CLASS = 6, TAG_CACC = 7 };
 
 /* ------------------------------------------------------------------------- */
 /* Model (Sec. 2.1).                                                          */
@@ -486,6 +488,58 @@ int orc_sweep_tilesets(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32
         }
     free(tile_order);
     free(cell_order);
+    return 0;
+}
+
+/* Random-sequential updates by colour classes (a parallel reference for the
+ * random-sequential dynamics, no decomposition): sweep s is K = 4 * 2^m
+ * sub-steps i; sub-step i draws one of the four period-2 sublattices,
+ *   c = philox(6<<28 | i, 0xffffffff, s, sample).w0 & 3, sites x = c & 1,
+ *   y = c >> 1 (mod 2),
+ * and attempts each of its sites with probability 2^-m. Sites of one class
+ * are never neighbours, so the attempts of a sub-step commute, and as m grows
+ * the dynamics approaches random-sequential updates (each site one attempt
+ * per sweep on average). Bit layout of the draws: 128 x 128 tiles anchored at
+ * (0, 0), tile T = ty * (L/128) + tx; cell row cy = v >> 2, storage cell
+ * c4 = u >> 2 (u, v tile-local), class site a = 2 ((v >> 1) & 1) + ((u >> 1) & 1):
+ *   selected iff bit c4 of S[0] & ... & S[m-1], S = philox(6<<28 | i << 9 |
+ *   cy << 2 | a, T, s, sample) (m <= 4);
+ *   acceptance U (16 bits, level 0 most significant), level n from bit c4 of
+ *   A_{n>>2}[n&3], A_k = philox(7<<28 | i << 9 | cy << 4 | a << 2 | k, T, s, sample).
+ * Needs L >= 128. Returns 0, or -1 on bad input. */
+int orc_sweep_colour(uint32_t L, uint32_t Tp, uint32_t Tq, uint32_t m, uint64_t seed, uint32_t sample,
+                     uint32_t s, uint8_t* sx, uint8_t* sy, int64_t* h00) {
+    if (L < 128 || (L & (L - 1)) || m > 4 || Tp > 65536u || Tq > 65536u) return -1;
+    const uint32_t B = 128, ntx = L / B, K = 4u << m;
+    memo msel = {0}, macc[4] = {{0}};
+    for (uint32_t i = 0; i < K; ++i) {
+        uint32_t w[4];
+        philox_at(((uint32_t)TAG_CLASS << 28) | i, 0xffffffffu, s, sample, seed, w);
+        uint32_t c = w[0] & 3u, cx = c & 1u, cyc = c >> 1;
+        for (uint32_t j = cyc; j < L; j += 2)
+            for (uint32_t x = cx; x < L; x += 2) {
+                uint32_t T = (j / B) * ntx + x / B, u = x % B, v = j % B;
+                uint32_t c4 = u >> 2, cy = v >> 2, a = 2 * ((v >> 1) & 1u) + ((u >> 1) & 1u);
+                uint32_t sel = 1;
+                if (m) {
+                    const uint32_t* S = memo_philox(&msel, ((uint32_t)TAG_CLASS << 28) | (i << 9) | (cy << 2) | a,
+                                                    T, s, sample, seed);
+                    uint32_t word = ~0u;
+                    for (uint32_t k = 0; k < m; ++k) word &= S[k];
+                    sel = (word >> c4) & 1u;
+                }
+                if (!sel) continue;
+                uint32_t U = 0;
+                for (uint32_t lev = 0; lev < 16; ++lev) {
+                    uint32_t mi = lev >> 2;
+                    const uint32_t* A = memo_philox(&macc[mi], ((uint32_t)TAG_CACC << 28) | (i << 9) | (cy << 4) |
+                                                    (a << 2) | mi, T, s, sample, seed);
+                    U |= ((A[lev & 3u] >> c4) & 1u) << (15 - lev);
+                }
+                int dh = orc_attempt(L, sx, sy, x, j, U < Tp, U < Tq);
+                if (dh != 0 && x == 0 && j == 0 && h00) *h00 += dh;
+            }
+    }
     return 0;
 }
 

@@ -91,6 +91,9 @@ def lib():
                                        c.c_uint64, c.c_uint32, c.c_uint32, u8p, u8p,
                                        c.POINTER(c.c_int64), c.c_uint64]
             L.orc_sweep_c2.restype = c.c_int
+            L.orc_sweep_colour.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint64,
+                                           c.c_uint32, c.c_uint32, u8p, u8p, c.POINTER(c.c_int64)]
+            L.orc_sweep_colour.restype = c.c_int
             _lib = L
     return _lib
 
@@ -179,6 +182,18 @@ class State:
         h = ctypes.c_int64(self.h00)
         rc = lib().orc_sweep_c2(self.L, Bx, By, threshold(p), threshold(q), seed, sample, self.t,
                                 self.sx, self.sy, ctypes.byref(h), order)
+        if rc:
+            raise ValueError("invalid oracle parameters")
+        self.h00 = h.value
+        self.t += 1
+        return self
+
+    def sweep_colour(self, p, q, seed, sample=0, m=3):
+        """One sweep of random-sequential updates by colour classes (4 * 2^m
+        sub-steps, each a random 2^-m subset of one period-2 sublattice)."""
+        h = ctypes.c_int64(self.h00)
+        rc = lib().orc_sweep_colour(self.L, threshold(p), threshold(q), m, seed, sample, self.t,
+                                    self.sx, self.sy, ctypes.byref(h))
         if rc:
             raise ValueError("invalid oracle parameters")
         self.h00 = h.value
