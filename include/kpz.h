@@ -81,13 +81,19 @@ typedef struct {
                              swept one set at a time in an order drawn per sweep
                              from Philox (tag 5), no dead border. 1 needs
                              128 x 128 tiles and L >= 256. The work-group layer
-                             (single-hit double tiling) is the same in both.   */
+                             (single-hit double tiling) is the same in both.
+                             2 = no decomposition: the random-sequential
+                             reference by colour classes (4 * 2^m sub-steps per
+                             sweep, each attempting a random 2^-m subset of one
+                             period-2 sublattice, m = colour_sparsity)        */
     uint32_t cell;        /* work-group layer cell edge (Sec. 3.1): 4 (0 = 4):
                              4 x 4 cells, 2 x 2 quadrant sets, 16 rounds per
                              sweep; or 2: the C = 2 limit, 2 x 2 cells whose
                              1 x 1 quadrants are the sets, 4 rounds per sweep,
                              no position draw (needs 128 x 128 tiles and
                              decomposition 0)                                  */
+    uint32_t colour_sparsity; /* decomposition 2: m in 1..4 (0 = 3); the bias
+                             against one attempt at a time is of order 2^-m   */
 } kpz_opts;
 
 /* Roughness at the current time (eq. Wdef). Heights are taken in the gauge
@@ -150,7 +156,7 @@ kpz_status kpz_set_slopes(kpz_ctx* ctx, const uint32_t* host_in, int64_t h00, ui
  * the file `path` (created or truncated):
  *   header   "KPZCKPT1", version 1, L, p, q (as given to kpz_init), the
  *            thresholds Tp, Tq, seed, sample, tile shape (bx, by), the device-layer
- *            decomposition and cell edge (kpz_opts.decomposition, .cell), the sweep
+ *            decomposition, cell edge and colour sparsity (kpz_opts), the sweep
  *            counter t_mcs and the absolute height of site (0,0);
  *   payload  the lattice in the packed exchange format (L*L/16 uint32,
  *            row-major, as kpz_slopes), written in bands;

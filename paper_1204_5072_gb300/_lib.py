@@ -26,7 +26,8 @@ class kpz_opts(ctypes.Structure):
     _fields_ = [("bx", ctypes.c_uint32), ("by", ctypes.c_uint32), ("run", ctypes.c_uint32),
                 ("warps_per_cta", ctypes.c_uint32), ("stream", ctypes.c_void_p),
                 ("dev_buf", ctypes.c_void_p), ("dev_bytes", ctypes.c_size_t),
-                ("decomposition", ctypes.c_uint32), ("cell", ctypes.c_uint32)]
+                ("decomposition", ctypes.c_uint32), ("cell", ctypes.c_uint32),
+                ("colour_sparsity", ctypes.c_uint32)]
 
 
 class kpz_rough(ctypes.Structure):
@@ -119,12 +120,12 @@ class Lattice:
 
     def __init__(self, L: int, p: float = 1.0, q: float = 0.0, seed: int = 1, sample: int = 0,
                  run: int = 0, warps_per_cta: int = 0, stream=None, device_buffer=None,
-                 tile_y: int = 0, decomposition: int = 0, cell: int = 0):
+                 tile_y: int = 0, decomposition: int = 0, cell: int = 0, colour_sparsity: int = 0):
         lib = load()
         self.L, self.p, self.q, self.seed, self.sample = int(L), float(p), float(q), int(seed), int(sample)
         o = kpz_opts()
         o.run, o.warps_per_cta, o.by = run, warps_per_cta, tile_y
-        o.decomposition, o.cell = decomposition, cell
+        o.decomposition, o.cell, o.colour_sparsity = decomposition, cell, colour_sparsity
         if stream is None:
             try:
                 import torch

@@ -28,6 +28,7 @@ struct kpz_ctx {
   uint32_t tile_y = 128;               // tile height in sites (128 or 256)
   uint32_t decomposition = 0;          // device layer: 0 dead border, 1 tile sets
   uint32_t cell = 4;                   // work-group cell edge: 4 or 2
+  uint32_t colour_m = 3;               // decomposition 2: subset sparsity
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_buf = false;
@@ -155,7 +156,9 @@ kpz_status kpz_init(kpz_ctx** out, uint32_t L, double p, double q, uint64_t seed
     return KPZ_EINVAL;
   kpz_opts o{};
   if (opts) o = *opts;
-  if (o.decomposition > 1u || (o.decomposition == 1u && ((o.by != 0 && o.by != kTile) || L < 2u * kTile)))
+  if (o.decomposition > 2u || (o.decomposition == 1u && ((o.by != 0 && o.by != kTile) || L < 2u * kTile)) ||
+      (o.decomposition == 2u && ((o.by != 0 && o.by != kTile) || (o.cell != 0 && o.cell != 4u))) ||
+      o.colour_sparsity > 4u || (o.colour_sparsity != 0 && o.decomposition != 2u))
     return KPZ_EINVAL;
   if ((o.cell != 0 && o.cell != 4u && o.cell != 2u) ||
       (o.cell == 2u && (o.decomposition != 0u || (o.by != 0 && o.by != kTile))))
@@ -189,6 +192,7 @@ kpz_status kpz_init(kpz_ctx** out, uint32_t L, double p, double q, uint64_t seed
   ctx->tile_y = o.by ? o.by : kTile;
   ctx->decomposition = o.decomposition;
   ctx->cell = o.cell ? o.cell : 4u;
+  ctx->colour_m = o.colour_sparsity ? o.colour_sparsity : 3u;
   ctx->run = o.run ? o.run : std::min(8u, ntx);   // tiles per work-queue chunk
   ctx->wpc = o.warps_per_cta ? o.warps_per_cta : 8u;
   ctx->stream = (cudaStream_t)o.stream;
@@ -243,8 +247,9 @@ kpz_status kpz_run(kpz_ctx* ctx, uint64_t n_mcs) {
     const uint32_t chunk = (uint32_t)std::min<uint64_t>(n_mcs, 1u << 20);
     for (uint32_t i = 0; i < chunk; ++i) {
       P.s_add = i;
-      if (ctx->decomposition == 1u) KPZ_CUDA(launch_sweep_tilesets(P, ctx->stream));
-      else                          KPZ_CUDA(launch_sweep(P, ctx->wpc, ctx->stream));
+      if (ctx->decomposition == 1u)      KPZ_CUDA(launch_sweep_tilesets(P, ctx->stream));
+      else if (ctx->decomposition == 2u) KPZ_CUDA(launch_sweep_colour(P, ctx->colour_m, ctx->stream));
+      else                               KPZ_CUDA(launch_sweep(P, ctx->wpc, ctx->stream));
     }
     KPZ_CUDA(launch_advance(ctx->t_dev, chunk, ctx->stream));
     ctx->t_host += chunk;
@@ -390,7 +395,9 @@ kpz_status kpz_ckpt_save(kpz_ctx* ctx, const char* path) {
   hd.sample = ctx->sample;
   hd.bx = kTile;
   hd.by = ctx->tile_y;
-  hd.decomposition = ctx->decomposition | (ctx->cell == 2u ? 0x100u : 0u);   // bit 8: C = 2
+  // bits 0-7: device layer, bit 8: C = 2, bits 12-15: colour sparsity (decomposition 2)
+  hd.decomposition = ctx->decomposition | (ctx->cell == 2u ? 0x100u : 0u) |
+                     (ctx->decomposition == 2u ? ctx->colour_m << 12 : 0u);
   unsigned long long small[2];
   KPZ_CUDA(cudaMemcpyAsync(small, ctx->t_dev, sizeof(small), cudaMemcpyDeviceToHost, ctx->stream));
   KPZ_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -427,13 +434,17 @@ kpz_status kpz_ckpt_load(kpz_ctx** out, const char* path, const kpz_opts* opts) 
   CkptHeader hd{};
   if (fread(&hd, sizeof(hd), 1, in.f) != 1 || memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != 1 ||
       !valid_L(hd.L) || hd.bx != kTile || (hd.by != kTile && hd.by != 2u * kTile) ||
-      acceptance_threshold(hd.p) != hd.Tp || acceptance_threshold(hd.q) != hd.Tq || (hd.decomposition & ~0x100u) > 1u)
+      acceptance_threshold(hd.p) != hd.Tp || acceptance_threshold(hd.q) != hd.Tq || (hd.decomposition & ~0xF100u) > 2u)
     return KPZ_ECKPT;
   kpz_opts o{};
   if (opts) o = *opts;
   if ((o.bx != 0 && o.bx != hd.bx) || (o.by != 0 && o.by != hd.by)) return KPZ_EINVAL;
   const uint32_t dec = hd.decomposition & 0xFFu, cell = (hd.decomposition & 0x100u) ? 2u : 4u;
-  if ((o.decomposition != 0 && o.decomposition != dec) || (o.cell != 0 && o.cell != cell)) return KPZ_EINVAL;
+  const uint32_t cm = (hd.decomposition >> 12) & 0xFu;
+  if ((o.decomposition != 0 && o.decomposition != dec) || (o.cell != 0 && o.cell != cell) ||
+      (o.colour_sparsity != 0 && o.colour_sparsity != cm))
+    return KPZ_EINVAL;
+  o.colour_sparsity = dec == 2u ? cm : 0u;
   o.bx = hd.bx;
   o.by = hd.by;
   o.decomposition = dec;

@@ -50,6 +50,9 @@ cudaError_t launch_advance(uint64_t* t_dev, uint32_t n, cudaStream_t st);
 // One sweep of the tile-set variant of the device layer (kpz_tileset.cu):
 // four launches, one per tile set, in the order drawn for the sweep.
 cudaError_t launch_sweep_tilesets(const SweepParams& P, cudaStream_t st);
+// One sweep of the random-sequential reference by colour classes (kpz_colour.cu):
+// 4 * 2^m launches, one per sub-step.
+cudaError_t launch_sweep_colour(const SweepParams& P, uint32_t m, cudaStream_t st);
 
 // Observables and conversions (kpz_observe.cu).
 cudaError_t launch_init_flat(uint32_t* lat, Geometry g, cudaStream_t st);

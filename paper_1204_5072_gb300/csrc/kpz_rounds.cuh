@@ -53,7 +53,7 @@ __device__ __forceinline__ uint4 draw(const SweepParams& P, const TileCtx& tc, u
 
 // Bit-serial comparison U < T for the 32 cells of a cell row (U uniform
 // 16-bit, level n = bit 15-n of U taken from bit c of word n&3 of Philox call
-// n>>2, call m at counter word 0 = tag 3 << 28 | base | m). Only cells in needp (selected site is a minimum) and needq (a
+// n>>2, call m at counter word 0 = base | m; base holds the stream's tag). Only cells in needp (selected site is a minimum) and needq (a
 // maximum) need a decision; a cell is decided at the first level where U and
 // T differ, so the warp stops drawing levels once no cell of any lane is still
 // tied. The outcome equals the full 16-level comparison.
@@ -66,7 +66,7 @@ __device__ __forceinline__ void acceptance(const SweepParams& P, const TileCtx& 
 #pragma unroll 1
   for (uint32_t m = 0; m < 4; ++m) {
     if (4u * m >= P.nlev || !__any_sync(0xffffffffu, (undp | undq) != 0u)) break;
-    const uint4 A = draw<kSK>(P, tc, (kTagAcc << 28) | base | m);
+    const uint4 A = draw<kSK>(P, tc, base | m);
     const uint32_t w[4] = {A.x, A.y, A.z, A.w};
 #pragma unroll
     for (uint32_t j = 0; j < 4; ++j) {
@@ -204,7 +204,7 @@ __device__ __forceinline__ void one_round(uint32_t (&T)[CR][4][4], const uint32_
 #pragma unroll
   for (int row = 0; row < CR; ++row) {
     uint32_t AP, AQ;
-    acceptance<kSK>(P, tc, ((CR * lane + row) << 6) | (r << 2),
+    acceptance<kSK>(P, tc, (kTagAcc << 28) | ((CR * lane + row) << 6) | (r << 2),
                     fmin[row][0][0] | fmin[row][0][1] | fmin[row][1][0] | fmin[row][1][1],
                     fmax[row][0][0] | fmax[row][0][1] | fmax[row][1][0] | fmax[row][1][1], AP, AQ);
 #pragma unroll
@@ -284,7 +284,7 @@ __device__ __forceinline__ void c2_round(uint32_t (&T)[4][4], const uint32_t (&h
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
         uint32_t AP, AQ;
-        acceptance<kSK>(P, tc, (lane << 6) | (r << 4) | (uint32_t)((2 * j + i) << 2), fmin[j][i],
+        acceptance<kSK>(P, tc, (kTagAcc << 28) | (lane << 6) | (r << 4) | (uint32_t)((2 * j + i) << 2), fmin[j][i],
                         fmax[j][i], AP, AQ);
         fmin[j][i] &= AP;
         fmax[j][i] &= AQ;
