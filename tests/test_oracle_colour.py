@@ -44,3 +44,36 @@ def test_thin_subsets_approach_random_sequential_updates():
     # whole sublattices at once: from the flat start at p = 1 a class of minima
     # rises together, which keeps the surface nearly flat
     assert abs(ms[-1] - mr[-1]) > 0.5 * mr[-1], (ms, mr)
+
+
+def _sync_by_heights(h, classes, p, q):
+    """Whole sublattices at once, on heights: for each class (cx, cy) in turn,
+    every site (x, y) with x = cx, y = cy mod 2 that is a local minimum rises
+    by 2 (if p) and every local maximum falls by 2 (if q) (eq. rule, Sec. 2.1),
+    all of them simultaneously; heights indexed [y, x], periodic."""
+    h = h.copy()
+    for c in classes:
+        cx, cy = c & 1, c >> 1
+        nb = [np.roll(h, 1, 0), np.roll(h, -1, 0), np.roll(h, 1, 1), np.roll(h, -1, 1)]
+        lo = np.all([n > h for n in nb], axis=0)
+        hi = np.all([n < h for n in nb], axis=0)
+        on = np.zeros_like(lo)
+        on[cy::2, cx::2] = True
+        h = h + 2 * (lo & on & (p == 1.0)) - 2 * (hi & on & (q == 1.0))
+    return h
+
+
+@pytest.mark.parametrize("p,q", [(1.0, 0.0), (0.0, 1.0), (1.0, 1.0)])
+def test_synchronous_limit_equals_sublattice_updates_on_heights(p, q):
+    """At m = 0 every site of the drawn class is attempted and acceptance is
+    certain, so a sweep is four synchronous sublattice updates; the classes
+    come from philox(6 << 28 | i, 0xffffffff, s, sample). Checked on absolute
+    heights, independently of the oracle's slope representation."""
+    L, seed, sample = 128, 11, 2
+    st = O.State.flat(L)
+    h = st.heights(absolute=True)
+    for s in range(5):
+        classes = [int(O.philox([(6 << 28) | i, 0xFFFFFFFF, s, sample], [seed, 0])[0]) & 3 for i in range(4)]
+        h = _sync_by_heights(h, classes, p, q)
+        st.sweep_colour(p, q, seed, sample, m=0)
+        assert np.array_equal(st.heights(absolute=True), h), s
