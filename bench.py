@@ -488,25 +488,35 @@ def main():
         host_in.reshape(L, L // 16)[1::2] = 0xCCCCCCCC
         host_out = torch.empty(nwords, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
 
+        parts = []   # host clock at the boundaries; every call returns after its stream work
+
         def e2e_step():
+            c0 = time.perf_counter()
             lat.set_slopes(host_in, h00=0, t=0)
+            c1 = time.perf_counter()
             t_prev = 0
             for t in times:
                 if t - t_prev:
                     lat.run(t - t_prev)
                 lat.roughness()
                 t_prev = t
+            c2 = time.perf_counter()
             lat.slopes_into(host_out)
+            parts.append((c1 - c0, c2 - c1, time.perf_counter() - c2))
 
         e2e_step()
         barrier()
+        parts.clear()
         t0 = time.perf_counter()
         for _ in range(a.steps):
             e2e_step()
         barrier()
         e2e_dt = max_over_ranks(time.perf_counter() - t0, dist)
+        med = np.median(np.array(parts), axis=0) * 1e3
         e2e = {"value": attempts / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": nwords * 4,
-               "d2h_bytes_per_step": nwords * 4 + len(times) * 48}
+               "d2h_bytes_per_step": nwords * 4 + len(times) * 48,
+               "parts_ms": {"import": round(float(med[0]), 2), "job": round(float(med[1]), 2),
+                            "export": round(float(med[2]), 2)}}
 
     cpu = cpu_mt = None
     if rank == 0 and world == 1 and not a.no_cpu:

@@ -43,6 +43,11 @@ struct kpz_ctx {
   int32_t* col0 = nullptr;             // h(0,j)
   void* io = nullptr;                  // staging band for host transfers
   size_t io_bytes = 0;
+  // Slope import/export: copies on io_stream overlap the conversion kernels
+  // on `stream`, the staging band split into two halves. Events: [0..1] half
+  // filled (copy done / kernel done), [2..3] half free, [4] stream -> io_stream.
+  cudaStream_t io_stream = nullptr;
+  cudaEvent_t io_ev[5] = {};
   uint64_t t_host = 0;
   bool poisoned = false;
   std::string err;
@@ -98,6 +103,27 @@ kpz_status enter(kpz_ctx* ctx) {
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
   return KPZ_OK;
+}
+
+// Creates the copy stream and events on first use and orders io_stream after
+// the work already queued on the context's stream.
+cudaError_t io_prepare(kpz_ctx* c) {
+  cudaError_t e = cudaSuccess;
+  if (!c->io_stream) {
+    e = cudaStreamCreateWithFlags(&c->io_stream, cudaStreamNonBlocking);
+    for (int i = 0; i < 5 && e == cudaSuccess; ++i)
+      e = cudaEventCreateWithFlags(&c->io_ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  e = cudaEventRecord(c->io_ev[4], c->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->io_stream, c->io_ev[4], 0);
+  return e;
+}
+
+// Rows per band when the staging band is used as two halves.
+uint32_t io_band_rows(const kpz_ctx* c, size_t row_bytes, size_t* half) {
+  *half = (c->io_bytes / 2) / kAlign * kAlign;
+  return (uint32_t)std::min<size_t>(c->g.L, *half / row_bytes) & ~3u;
 }
 
 SweepParams sweep_params(const kpz_ctx* c) {
@@ -307,14 +333,22 @@ kpz_status kpz_slopes(kpz_ctx* ctx, uint32_t* host_out) {
   if (!host_out) return fail(ctx, KPZ_EINVAL, "null output");
   const uint32_t L = ctx->g.L;
   const size_t row_bytes = (size_t)L / 16 * 4;
-  const uint32_t band = (uint32_t)std::min<size_t>(L, ctx->io_bytes / row_bytes) & ~3u;
-  for (uint32_t j0 = 0; j0 < L; j0 += band) {
-    const uint32_t nr = std::min(band, L - j0);
-    KPZ_CUDA(launch_export_packed(ctx->lat, ctx->g, j0, nr, (uint32_t*)ctx->io, ctx->stream));
-    KPZ_CUDA(cudaMemcpyAsync((char*)host_out + (size_t)j0 * row_bytes, ctx->io, nr * row_bytes,
-                             cudaMemcpyDeviceToHost, ctx->stream));
-    KPZ_CUDA(cudaStreamSynchronize(ctx->stream));
+  size_t half = 0;
+  const uint32_t band = io_band_rows(ctx, row_bytes, &half);
+  char* buf[2] = {(char*)ctx->io, (char*)ctx->io + half};
+  KPZ_CUDA(io_prepare(ctx));
+  uint32_t b = 0;
+  for (uint32_t j0 = 0; j0 < L; j0 += band, ++b) {
+    const uint32_t nr = std::min(band, L - j0), k = b & 1u;
+    if (b >= 2) KPZ_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->io_ev[2 + k], 0));   // half k read out
+    KPZ_CUDA(launch_export_packed(ctx->lat, ctx->g, j0, nr, (uint32_t*)buf[k], ctx->stream));
+    KPZ_CUDA(cudaEventRecord(ctx->io_ev[k], ctx->stream));
+    KPZ_CUDA(cudaStreamWaitEvent(ctx->io_stream, ctx->io_ev[k], 0));
+    KPZ_CUDA(cudaMemcpyAsync((char*)host_out + (size_t)j0 * row_bytes, buf[k], nr * row_bytes,
+                             cudaMemcpyDeviceToHost, ctx->io_stream));
+    KPZ_CUDA(cudaEventRecord(ctx->io_ev[2 + k], ctx->io_stream));
   }
+  KPZ_CUDA(cudaStreamSynchronize(ctx->io_stream));
   return KPZ_OK;
 }
 
@@ -324,18 +358,25 @@ kpz_status kpz_set_slopes(kpz_ctx* ctx, const uint32_t* host_in, int64_t h00, ui
   if (!host_in) return fail(ctx, KPZ_EINVAL, "null input");
   const uint32_t L = ctx->g.L;
   const size_t row_bytes = (size_t)L / 16 * 4;
-  const uint32_t band = (uint32_t)std::min<size_t>(L, ctx->io_bytes / row_bytes) & ~3u;
+  size_t half = 0;
+  const uint32_t band = io_band_rows(ctx, row_bytes, &half);
+  char* buf[2] = {(char*)ctx->io, (char*)ctx->io + half};
   ctx->g.par = (uint32_t)(h00 & 1);
   const uint32_t h00_mod4 = (uint32_t)(h00 & 3);
   KPZ_CUDA(cudaMemcpyAsync(ctx->hcar, &h00_mod4, sizeof(uint32_t), cudaMemcpyHostToDevice,
                            ctx->stream));
-  for (uint32_t j0 = 0; j0 < L; j0 += band) {
-    const uint32_t nr = std::min(band, L - j0);
-    KPZ_CUDA(cudaMemcpyAsync(ctx->io, (const char*)host_in + (size_t)j0 * row_bytes, nr * row_bytes,
-                             cudaMemcpyHostToDevice, ctx->stream));
-    KPZ_CUDA(launch_import_packed(ctx->lat, ctx->g, j0, nr, (const uint32_t*)ctx->io, ctx->hcar,
+  KPZ_CUDA(io_prepare(ctx));
+  uint32_t b = 0;
+  for (uint32_t j0 = 0; j0 < L; j0 += band, ++b) {
+    const uint32_t nr = std::min(band, L - j0), k = b & 1u;
+    if (b >= 2) KPZ_CUDA(cudaStreamWaitEvent(ctx->io_stream, ctx->io_ev[2 + k], 0));   // half k converted
+    KPZ_CUDA(cudaMemcpyAsync(buf[k], (const char*)host_in + (size_t)j0 * row_bytes, nr * row_bytes,
+                             cudaMemcpyHostToDevice, ctx->io_stream));
+    KPZ_CUDA(cudaEventRecord(ctx->io_ev[k], ctx->io_stream));
+    KPZ_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->io_ev[k], 0));
+    KPZ_CUDA(launch_import_packed(ctx->lat, ctx->g, j0, nr, (const uint32_t*)buf[k], ctx->hcar,
                                   ctx->col0, ctx->stream));
-    KPZ_CUDA(cudaStreamSynchronize(ctx->stream));
+    KPZ_CUDA(cudaEventRecord(ctx->io_ev[2 + k], ctx->stream));
   }
   unsigned long long small[2] = {(unsigned long long)t_mcs, (unsigned long long)h00};
   KPZ_CUDA(cudaMemcpyAsync(ctx->t_dev, small, sizeof(small), cudaMemcpyHostToDevice, ctx->stream));
@@ -495,6 +536,12 @@ kpz_status kpz_device_lattice(kpz_ctx* ctx, void** dev_ptr, size_t* bytes) {
 void kpz_free(kpz_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
+  if (ctx->io_stream) {
+    cudaStreamSynchronize(ctx->io_stream);
+    for (cudaEvent_t ev : ctx->io_ev)
+      if (ev) cudaEventDestroy(ev);
+    cudaStreamDestroy(ctx->io_stream);
+  }
   if (ctx->own_buf && ctx->buf) {
     cudaStreamSynchronize(ctx->stream);
     cudaFree(ctx->buf);

@@ -44,29 +44,51 @@ __device__ __forceinline__ uint32_t part1by1(uint32_t a) {
   return a;
 }
 
-// One packed word (16 sites of row j) per thread.
-__global__ void export_kernel(const uint32_t* __restrict__ lat, Geometry g, uint32_t j0,
-                              uint32_t nrows, uint32_t* __restrict__ packed) {
-  const uint32_t wpr = g.L / 16;
-  const size_t n = (size_t)nrows * wpr;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t j = j0 + (uint32_t)(idx / wpr), wi = (uint32_t)(idx % wpr);
-    const uint32_t j1 = (j + 1u) & (g.L - 1u);
-    const uint32_t K = wi >> 3, c0 = (wi & 7u) * 4u;
-    uint32_t r0 = 0, r1 = 0;  // bits of sites 16wi + k, k = 0..15, rows j and j+1
+// Block columns of one import/export block: warp w of a block takes block
+// columns [w KS, (w + 1) KS), KS = NB / min(kIoSegs, NB).
+constexpr uint32_t kIoSegs = 16;
+
+// Rows j = 4R + y4 of a band for 32 consecutive cell rows R (lane = R - R0)
+// and one y4 (blockIdx.x = 4 group + y4): a warp's loads of one plane word are
+// 128 contiguous bytes, and each lane writes its row's 8 packed words of a
+// block column (32 contiguous bytes).
+__global__ void __launch_bounds__(32 * kIoSegs) export_kernel(const uint32_t* __restrict__ lat, Geometry g,
+                                                              uint32_t j0, uint32_t nrows,
+                                                              uint32_t* __restrict__ packed) {
+  const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+  const uint32_t S = min(kIoSegs, g.NB), KS = g.NB / S;
+  const uint32_t y4 = blockIdx.x & 3u, rr = 32u * (blockIdx.x >> 2) + lane;
+  if (w >= S || 4u * rr >= nrows) return;
+  const uint32_t R = j0 / 4u + rr, j = 4u * R + y4;
+  const uint32_t y4n = (y4 + 1u) & 3u, Rn = (y4 == 3u) ? ((R + 1u) & (g.NR - 1u)) : R;   // row j + 1
+  // parity of site 16 wi + k is (k + j + par) & 1; a neighbour is higher iff
+  // the bits differ by that parity, so sigma = +1 <=> b(next) ^ b ^ parity == 0
+  const uint32_t odd = ((j + g.par) & 1u) ? 0x5555u : 0xAAAAu;
+  uint4* out = reinterpret_cast<uint4*>(packed + (size_t)(4u * rr + y4) * (g.L / 16u));
+  for (uint32_t K = w * KS; K < (w + 1u) * KS; ++K) {
+    uint32_t A[4], B[4];
 #pragma unroll
     for (uint32_t x4 = 0; x4 < 4; ++x4) {
-      r0 |= spread4((lat[g.word(K, plane(j & 3u, x4), j >> 2)] >> c0) & 0xFu) << x4;
-      r1 |= spread4((lat[g.word(K, plane(j1 & 3u, x4), j1 >> 2)] >> c0) & 0xFu) << x4;
+      A[x4] = lat[g.word(K, plane(y4, x4), R)];
+      B[x4] = lat[g.word(K, plane(y4n, x4), Rn)];
     }
-    r0 |= site_bit(lat, g, (16u * wi + 16u) & (g.L - 1u), j) << 16;
-    // parity of site 16wi + k is (k + j + par) & 1; higher neighbour <=> bits
-    // differ by that parity, so sigma = +1 <=> b(next) ^ b ^ parity == 0
-    const uint32_t odd = ((j + g.par) & 1u) ? 0x5555u : 0xAAAAu;
-    const uint32_t sx = ~((r0 >> 1) ^ r0 ^ odd) & 0xFFFFu;
-    const uint32_t sy = ~(r1 ^ r0 ^ odd) & 0xFFFFu;
-    packed[idx] = part1by1(sx) | (part1by1(sy) << 1);
+    const uint32_t nxt = lat[g.word((K + 1u) & (g.NB - 1u), plane(y4, 0), R)] & 1u;   // site 128(K+1)
+    uint32_t o[8];
+#pragma unroll
+    for (uint32_t q = 0; q < 8; ++q) {   // packed word q: sites 16q + k = cells 4q + k/4, x4 = k%4
+      uint32_t r0 = 0, r1 = 0;
+#pragma unroll
+      for (uint32_t x4 = 0; x4 < 4; ++x4) {
+        r0 |= spread4((A[x4] >> (4u * q)) & 0xFu) << x4;
+        r1 |= spread4((B[x4] >> (4u * q)) & 0xFu) << x4;
+      }
+      r0 |= (q < 7u ? (A[0] >> (4u * q + 4u)) & 1u : nxt) << 16;
+      const uint32_t sx = ~((r0 >> 1) ^ r0 ^ odd) & 0xFFFFu;
+      const uint32_t sy = ~(r1 ^ r0 ^ odd) & 0xFFFFu;
+      o[q] = part1by1(sx) | (part1by1(sy) << 1);
+    }
+    out[2u * K] = make_uint4(o[0], o[1], o[2], o[3]);
+    out[2u * K + 1u] = make_uint4(o[4], o[5], o[6], o[7]);
   }
 }
 
@@ -99,27 +121,71 @@ __global__ void import_col_kernel(const uint32_t* __restrict__ packed, Geometry 
   if (t == nt - 1) *hcar = (uint32_t)((base + part[nt - 1]) & 3);
 }
 
-// One row of a packed band per thread: walk along the row and store the bits.
-__global__ void import_rows_kernel(uint32_t* __restrict__ lat, Geometry g, uint32_t j0,
-                                   uint32_t nrows, const uint32_t* __restrict__ packed,
-                                   const int32_t* __restrict__ hcol) {
-  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nrows) return;
-  const uint32_t j = j0 + r, wpr = g.L / 16;
-  const uint32_t* row = packed + (size_t)r * wpr;
-  int32_t h = hcol[r];
-  for (uint32_t K = 0; K < g.NB; ++K) {
+// The 16 x-slopes of a packed word (its even bits) at bits 0..15.
+__device__ __forceinline__ uint32_t even_bits(uint32_t a) {
+  a &= 0x55555555u;
+  a = (a | (a >> 1)) & 0x33333333u;
+  a = (a | (a >> 2)) & 0x0F0F0F0Fu;
+  a = (a | (a >> 4)) & 0x00FF00FFu;
+  return (a | (a >> 8)) & 0x0000FFFFu;
+}
+
+// Bits 0, 4, 8, 12 of v at bits 0..3.
+__device__ __forceinline__ uint32_t gather4(uint32_t v) {
+  v &= 0x1111u;
+  v = (v | (v >> 3)) & 0x0303u;
+  return (v | (v >> 6)) & 0xFu;
+}
+
+// Bits of the rows of a packed band, laid out as in export_kernel. Along row
+// j, h(i,j) = h(0,j) - i + 2 U(i,j) with U(i,j) the number of +1 x-slopes
+// left of i, so b(i,j) = bit 1 of (h(0,j) - i) mod 4, XOR U(i,j) mod 2: a
+// prefix XOR of the x-slope bits. Each warp first takes the parity of its
+// block columns' x-slopes; the parities of the segments before it give its
+// carry.
+__global__ void __launch_bounds__(32 * kIoSegs) import_rows_kernel(uint32_t* __restrict__ lat, Geometry g,
+                                                                   uint32_t j0, uint32_t nrows,
+                                                                   const uint32_t* __restrict__ packed,
+                                                                   const int32_t* __restrict__ hcol) {
+  __shared__ uint32_t seg_par[kIoSegs][32];
+  const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+  const uint32_t S = min(kIoSegs, g.NB), KS = g.NB / S;
+  const uint32_t y4 = blockIdx.x & 3u, rr = 32u * (blockIdx.x >> 2) + lane;
+  const bool live = w < S && 4u * rr < nrows;
+  const uint32_t r = 4u * rr + y4;   // row within the band
+  const uint4* row = reinterpret_cast<const uint4*>(packed + (size_t)(live ? r : 0u) * (g.L / 16u));
+  uint32_t x = 0;
+  if (live)
+    for (uint32_t K = w * KS; K < (w + 1u) * KS; ++K) {
+      const uint4 a = row[2u * K], b = row[2u * K + 1u];
+      x ^= a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w;
+    }
+  seg_par[w][lane] = __popc(x & 0x55555555u) & 1u;
+  __syncthreads();
+  if (!live) return;
+  uint32_t carry = 0;   // parity of the +1 x-slopes left of the segment
+  for (uint32_t v = 0; v < w; ++v) carry ^= seg_par[v][lane];
+  // bit 1 of (h(0,j) - k) mod 4 for k = 0..15 (period 4; 16 wi = 0 mod 4)
+  const uint32_t pat = ((0x39C6u >> (4u * ((uint32_t)hcol[r] & 3u))) & 0xFu) * 0x1111u;
+  const uint32_t R = j0 / 4u + rr;
+  for (uint32_t K = w * KS; K < (w + 1u) * KS; ++K) {
+    const uint4 a = row[2u * K], b = row[2u * K + 1u];
+    const uint32_t pw[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
     uint32_t W[4] = {0u, 0u, 0u, 0u};
-    for (uint32_t q = 0; q < 8; ++q) {
-      const uint32_t pw = row[8u * K + q];
 #pragma unroll
-      for (uint32_t k = 0; k < 16; ++k) {  // site 128K + 16q + k = cell 4q + k/4, x4 = k%4
-        W[k & 3u] |= (uint32_t)((h >> 1) & 1) << (4u * q + (k >> 2));
-        h += ((pw >> (2u * k)) & 1u) ? 1 : -1;
-      }
+    for (uint32_t q = 0; q < 8; ++q) {   // sites 128K + 16q + k = cell 4q + k/4, x4 = k%4
+      uint32_t e = even_bits(pw[q]);
+      e ^= e << 1;
+      e ^= e << 2;
+      e ^= e << 4;
+      e ^= e << 8;                       // bit k: parity of the x-slopes 0..k of the word
+      const uint32_t bits = (((e << 1) ^ (0u - carry)) & 0xFFFFu) ^ pat;
+      carry ^= (e >> 15) & 1u;
+#pragma unroll
+      for (uint32_t x4 = 0; x4 < 4; ++x4) W[x4] |= gather4(bits >> x4) << (4u * q);
     }
 #pragma unroll
-    for (uint32_t x4 = 0; x4 < 4; ++x4) lat[g.word(K, plane(j & 3u, x4), j >> 2)] = W[x4];
+    for (uint32_t x4 = 0; x4 < 4; ++x4) lat[g.word(K, plane(y4, x4), R)] = W[x4];
   }
 }
 
@@ -285,9 +351,11 @@ cudaError_t launch_init_flat(uint32_t* lat, Geometry g, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Both conversions take j0 and nrows as multiples of 4 (whole cell rows) and a
+// 16-byte aligned packed band.
 cudaError_t launch_export_packed(const uint32_t* lat, Geometry g, uint32_t j0, uint32_t nrows,
                                  uint32_t* packed, cudaStream_t st) {
-  export_kernel<<<grid_for((size_t)nrows * (g.L / 16), 256), 256, 0, st>>>(lat, g, j0, nrows, packed);
+  export_kernel<<<4u * ((nrows / 4u + 31u) / 32u), 32u * kIoSegs, 0, st>>>(lat, g, j0, nrows, packed);
   count_launch();
   return cudaGetLastError();
 }
@@ -297,7 +365,7 @@ cudaError_t launch_import_packed(uint32_t* lat, Geometry g, uint32_t j0, uint32_
                                  cudaStream_t st) {
   import_col_kernel<<<1, 1024, 0, st>>>(packed, g, nrows, hcar, hcol);
   count_launch();
-  import_rows_kernel<<<(nrows + 127) / 128, 128, 0, st>>>(lat, g, j0, nrows, packed, hcol);
+  import_rows_kernel<<<4u * ((nrows / 4u + 31u) / 32u), 32u * kIoSegs, 0, st>>>(lat, g, j0, nrows, packed, hcol);
   count_launch();
   return cudaGetLastError();
 }
