@@ -483,10 +483,12 @@ def main():
     e2e = None
     if not a.no_e2e:
         nwords = L * L // 16
-        host_in = torch.empty(nwords, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+        h_in = torch.empty(nwords, dtype=torch.int32, pin_memory=True)
+        h_out = torch.empty(nwords, dtype=torch.int32, pin_memory=True)
+        host_in = h_in.numpy().view(np.uint32)
         host_in.reshape(L, L // 16)[0::2] = 0x33333333
         host_in.reshape(L, L // 16)[1::2] = 0xCCCCCCCC
-        host_out = torch.empty(nwords, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+        host_out = h_out.numpy().view(np.uint32)
 
         parts = []   # host clock at the boundaries; every call returns after its stream work
 
@@ -513,10 +515,27 @@ def main():
         barrier()
         e2e_dt = max_over_ranks(time.perf_counter() - t0, dist)
         med = np.median(np.array(parts), axis=0) * 1e3
+        # The bare pinned-memory copies of the same buffers in this process, for
+        # reading the import/export parts (host links differ from box to box).
+        dev_tmp = torch.empty(nwords, dtype=torch.int32, device="cuda")
+        link = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            c0 = time.perf_counter()
+            dev_tmp.copy_(h_in, non_blocking=True)
+            torch.cuda.synchronize()
+            c1 = time.perf_counter()
+            h_out.copy_(dev_tmp, non_blocking=True)
+            torch.cuda.synchronize()
+            link.append((c1 - c0, time.perf_counter() - c1))
+        del dev_tmp
+        best = np.min(np.array(link), axis=0)
         e2e = {"value": attempts / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": nwords * 4,
                "d2h_bytes_per_step": nwords * 4 + len(times) * 48,
                "parts_ms": {"import": round(float(med[0]), 2), "job": round(float(med[1]), 2),
-                            "export": round(float(med[2]), 2)}}
+                            "export": round(float(med[2]), 2)},
+               "bare_copy_gbs": {"h2d": round(nwords * 4 / best[0] / 1e9, 1),
+                                 "d2h": round(nwords * 4 / best[1] / 1e9, 1)}}
 
     cpu = cpu_mt = None
     if rank == 0 and world == 1 and not a.no_cpu:

@@ -66,9 +66,11 @@ typedef struct {
                              trajectories; 128 x 256 needs L >= 256               */
     uint32_t run;         /* tiles per work item: the resident warps take runs of
                              `run` tiles of one tile row from a queue (power of two
-                             <= L/128; 0 = min(8, L/128)); execution only, it does
-                             not change the result                                 */
-    uint32_t warps_per_cta; /* 1..8, 0 = 8; execution only                         */
+                             <= L/128; 0 = min(8, L/128) below L = 65536, L/4096
+                             from there); execution only, it does not change the
+                             result                                                */
+    uint32_t warps_per_cta; /* 1..8; 0 = 4 for 128-row tiles from L = 65536, else 8;
+                             execution only                                        */
     void* stream;         /* cudaStream_t to queue work on (NULL = default stream)  */
     void* dev_buf;        /* optional caller-owned device memory for the lattice and
                              its scratch; at least kpz_device_bytes(L) bytes,

@@ -219,8 +219,16 @@ kpz_status kpz_init(kpz_ctx** out, uint32_t L, double p, double q, uint64_t seed
   ctx->decomposition = o.decomposition;
   ctx->cell = o.cell ? o.cell : 4u;
   ctx->colour_m = o.colour_sparsity ? o.colour_sparsity : 3u;
-  ctx->run = o.run ? o.run : std::min(8u, ntx);   // tiles per work-queue chunk
-  ctx->wpc = o.warps_per_cta ? o.warps_per_cta : 8u;
+  // Default schedule, measured on GB300 at p = 1 (results do not depend on
+  // it): runs of 8 tiles and 8-warp CTAs up to 256 tiles per row; from 512
+  // tiles per row runs of ntx/32 tiles, which halve the per-run cost (window
+  // prologue, start copy, edge write-backs) while about 4.5 (L = 2^16) or 9
+  // (L = 2^17) runs per resident warp keep the last wave short, with 4-warp
+  // CTAs for 128-row tiles. L = 2^16: 0.4765 ms per sweep against 0.4954 ms;
+  // L = 2^17: 1.827 ms against 1.920 ms.
+  const bool wide = ntx >= 512u;
+  ctx->run = o.run ? o.run : (wide ? ntx / 32u : std::min(8u, ntx));   // tiles per work-queue chunk
+  ctx->wpc = o.warps_per_cta ? o.warps_per_cta : (wide && ctx->tile_y == kTile ? 4u : 8u);
   ctx->stream = (cudaStream_t)o.stream;
   if (o.dev_buf) {
     ctx->buf = o.dev_buf;

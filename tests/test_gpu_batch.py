@@ -141,3 +141,25 @@ def test_autotuned_tile_shape_is_reported_and_reproducible(eng):
     with pytest.raises(KpzError) as e:   # 128 x 256 tiles need L >= 256
         eng.Batch([(128, 1.0, 0.0, 1, 0, 3)], tile_y=256)
     assert e.value.status == KPZ_EINVAL
+
+
+def test_members_without_sweeps(eng):
+    """A member with zero sweeps is sampled once, at t = 0 (the flat start,
+    W^2 = 1/4 exactly, Sec. 2.1), and is NaN after; the others are unchanged.
+    A batch of such members alone has the single time t = 0."""
+    specs = [(256, 1.0, 0.0, 1, 0, 0), (128, 0.9, 0.1, 7, 3, 12), (128, 1.0, 0.0, 2, 1, 0)]
+    b = eng.Batch(specs, n_samples=6, timeout_ms=2000)
+    b.run()
+    times = [int(t) for t in b.times()]
+    w2 = b.w2()
+    s1, s2, h00 = b.sums()
+    for i in (0, 2):
+        assert w2[i, 0] == 0.25 and np.all(np.isnan(w2[i, 1:])) and h00[i] == 0
+    ref = _single(eng, *specs[1], times)
+    for k, t in enumerate(times):
+        assert (int(s1[1, k]), s2[1, k]) == ref[t][:2], t
+    b.close()
+    z = eng.Batch([(128, 1.0, 0.0, 1, 0, 0), (512, 0.5, 0.5, 3, 0, 0)], timeout_ms=2000)
+    z.run()
+    assert [int(t) for t in z.times()] == [0] and np.all(z.w2() == 0.25)
+    z.close()

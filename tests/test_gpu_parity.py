@@ -188,3 +188,15 @@ def test_tall_tiles_knobs_and_resume(eng):
     b.run(1)
     st.sweep(TILE, 2 * TILE, 0.9, 0.1, 12, 0)
     _same(b, st, "resume with By=256")
+
+
+def test_zero_sweeps_change_nothing(eng):
+    for L, p, q in [(128, 1.0, 0.0), (256, 0.8, 0.3)]:
+        lat = eng.Lattice(L, p, q, seed=5)
+        lat.run(0)
+        _same(lat, O.State.flat(L), f"L={L} t=0")
+        lat.run(3)
+        words, r = lat.slopes(), lat.roughness()
+        lat.run(0)
+        assert np.array_equal(lat.slopes(), words) and lat.roughness() == r
+        lat.close()
