@@ -56,7 +56,12 @@ struct kpz_ctx {
 namespace {
 
 constexpr size_t kAlign = 256;
+// Staging band for host transfers: the packed slope array (L^2/4 bytes) up to
+// 64 MiB. A slope import or export streams through its two halves, each copy
+// overlapping the conversion kernel of the other half; checkpoint file I/O
+// goes through a host buffer of the same size at most.
 constexpr size_t kIoMax = size_t(64) << 20;
+constexpr size_t kCkptHostMax = kIoMax;
 
 size_t align_up(size_t n) { return (n + kAlign - 1) / kAlign * kAlign; }
 
@@ -73,7 +78,7 @@ Layout layout(uint32_t L) {
   y.small = align_up(lat_bytes);                 // t, h00, acc[3], hcar, queue
   y.col0 = y.small + kAlign;
   y.io = y.col0 + align_up((size_t)L * 4);
-  const size_t io_bytes = std::min(kIoMax, (size_t)L * L * 8);
+  const size_t io_bytes = std::min(kIoMax, (size_t)L * L / 4);
   y.total = y.io + align_up(io_bytes);
   return y;
 }
@@ -458,7 +463,7 @@ kpz_status kpz_ckpt_save(kpz_ctx* ctx, const char* path) {
   uint64_t h = fnv_words(kFnvBasis, &hd, sizeof(hd));
   if (fwrite(&hd, sizeof(hd), 1, out.f) != 1) return fail(ctx, KPZ_ECKPT, "write failed");
   const size_t row_bytes = (size_t)L / 16 * 4;
-  const uint32_t band = (uint32_t)std::min<size_t>(L, ctx->io_bytes / row_bytes) & ~3u;
+  const uint32_t band = (uint32_t)std::min<size_t>(L, std::min(ctx->io_bytes, kCkptHostMax) / row_bytes) & ~3u;
   std::string host((size_t)band * row_bytes, '\0');
   for (uint32_t j0 = 0; j0 < L; j0 += band) {
     const uint32_t nr = std::min(band, L - j0);
@@ -505,7 +510,7 @@ kpz_status kpz_ckpt_load(kpz_ctx** out, const char* path, const kpz_opts* opts) 
   uint64_t h = fnv_words(kFnvBasis, &hd, sizeof(hd));
   const uint32_t L = hd.L;
   const size_t row_bytes = (size_t)L / 16 * 4;
-  const uint32_t band = (uint32_t)std::min<size_t>(L, ctx->io_bytes / row_bytes) & ~3u;
+  const uint32_t band = (uint32_t)std::min<size_t>(L, std::min(ctx->io_bytes, kCkptHostMax) / row_bytes) & ~3u;
   std::string host((size_t)band * row_bytes, '\0');
   ctx->g.par = (uint32_t)(hd.h00 & 1);
   const uint32_t h00_mod4 = (uint32_t)(hd.h00 & 3);

@@ -4,6 +4,8 @@ the first sweep against the oracle (tiles of one sweep do not interact, so
 the oracle computes each from the flat start on its own window), a valid
 surface (every row of sigma_x and every column of sigma_y sums to zero,
 Sec. 2.1) and the exact width computed a second, independent way."""
+import hashlib
+
 import numpy as np
 import pytest
 
@@ -77,6 +79,8 @@ def test_width_matches_host_recomputation(eng):
 
 
 def test_largest_lattice(eng):
+    """L = 2^17: valid surface after two sweeps, and the slopes round-trip
+    through an import into a second lattice (128 staging bands each way)."""
     L = 1 << 17
     lat = eng.Lattice(L, 1.0, 0.0, seed=3)
     lat.run(2)
@@ -85,6 +89,16 @@ def test_largest_lattice(eng):
     words = lat.slopes()
     w = words.reshape(L, L // 16)
     assert np.all(_popcount(w & np.uint32(0x55555555)).sum(axis=1, dtype=np.int64) == L // 2)
+    lat.close()
+    digest = hashlib.sha256(words.data).hexdigest()
+    b = eng.Lattice(L, 1.0, 0.0, seed=3)
+    b.set_slopes(words, h00=r["h00"], t=2)
+    rb = b.roughness()
+    assert (rb["S1"], rb["S2"], rb["h00"], rb["t"]) == (r["S1"], r["S2"], r["h00"], 2)
+    words[:] = 0
+    b.slopes_into(words)
+    assert hashlib.sha256(words.data).hexdigest() == digest
+    b.close()
 
 
 def _window(words, L, x0, y0, Bx, By):
