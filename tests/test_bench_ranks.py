@@ -54,3 +54,22 @@ def test_reference_arm_runs_on_rank_0_only(monkeypatch, capsys):
     monkeypatch.setenv("RANK", "1")
     bench.run_reference(type("A", (), {"gpus": 2, "steps": 1, "warmup": 3, "L": 65536, "mcs": 2000})())
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_prints_one_complete_line(monkeypatch, capsys):
+    """Rank 0 of the reference arm times the CPU oracle and prints exactly one
+    JSON line with the keys of the benchmark contract."""
+    import json
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    bench.run_reference(type("A", (), {"gpus": 1, "steps": 1, "warmup": 1, "L": 65536, "mcs": 2000})())
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["L"] == 65536
