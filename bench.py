@@ -224,6 +224,21 @@ def cpu_all_cores(mcs_sample: int):
             "sample": f"L={L}, {mcs_sample} MCS from the flat start + W^2", "seconds": dt}
 
 
+def cpu_rsu(mcs_sample: int):
+    """The oracle's random-sequential updates (one attempt at a uniformly random
+    site at a time, no decomposition: the dynamics the decomposition
+    approximates) on one core, L = 1024 from the flat start."""
+    from oracle import oracle as O
+    L, w = 1024, I.L65536_2000
+    st = O.State.flat(L)
+    t0 = time.perf_counter()
+    st.rsu(mcs_sample, w.p, w.q, w.seed, w.sample)
+    dt = time.perf_counter() - t0
+    return {"value": mcs_sample * L * L / dt, "unit": UNIT, "cores": 1,
+            "kind": "oracle, random-sequential updates",
+            "sample": f"L={L}, {mcs_sample} MCS from the flat start", "seconds": dt}
+
+
 # The paper's own update rates (order of magnitude from its text; its figures
 # are not available): context for the GB300 numbers, not a target.
 PAPER_CONTEXT = {"gpu_updates_per_s": 1e9,
@@ -537,10 +552,11 @@ def main():
                "bare_copy_gbs": {"h2d": round(nwords * 4 / best[0] / 1e9, 1),
                                  "d2h": round(nwords * 4 / best[1] / 1e9, 1)}}
 
-    cpu = cpu_mt = None
+    cpu = cpu_mt = cpu_seq = None
     if rank == 0 and world == 1 and not a.no_cpu:
         cpu = cpu_baseline(L, a.cpu_sample_mcs)
         cpu_mt = cpu_all_cores(max(10, a.cpu_sample_mcs // 2))
+        cpu_seq = cpu_rsu(max(4, a.cpu_sample_mcs // 10))
     batch = None if (a.no_batch or world > 1) else batch_bench(eng, a.batch_cap, n_specs=a.batch_n)
     sur = None if (a.no_surrogate or world > 1) else surrogate_bench(eng)
 
@@ -550,7 +566,7 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
                 "data": "synthetic (flat checkerboard start, p=1 q=0)",
                 "config": job_config(L, mcs, world),
-                "roofline": roofline, "cpu_baseline": cpu, "cpu_all_cores": cpu_mt,
+                "roofline": roofline, "cpu_baseline": cpu, "cpu_all_cores": cpu_mt, "cpu_rsu": cpu_seq,
                 "paper_context": PAPER_CONTEXT, "e2e": e2e,
                 "clocks": clk.summary(), "gpu_launches": launches,
                 "w2_final": rough[-1]["w2"], "batch": batch, "surrogate": sur}
