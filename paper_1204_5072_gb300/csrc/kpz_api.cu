@@ -115,10 +115,19 @@ kpz_status enter(kpz_ctx* ctx) {
 cudaError_t io_prepare(kpz_ctx* c) {
   cudaError_t e = cudaSuccess;
   if (!c->io_stream) {
-    e = cudaStreamCreateWithFlags(&c->io_stream, cudaStreamNonBlocking);
-    for (int i = 0; i < 5 && e == cudaSuccess; ++i)
-      e = cudaEventCreateWithFlags(&c->io_ev[i], cudaEventDisableTiming);
-    if (e != cudaSuccess) return e;
+    // All or nothing: on failure nothing is kept and the next call tries again.
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev[5] = {};
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+      if (s) cudaStreamDestroy(s);
+      return e;
+    }
+    c->io_stream = s;
+    for (int i = 0; i < 5; ++i) c->io_ev[i] = ev[i];
   }
   e = cudaEventRecord(c->io_ev[4], c->stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(c->io_stream, c->io_ev[4], 0);
