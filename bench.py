@@ -9,6 +9,14 @@ report updates per second). One JSON line on stdout (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
+Besides `value` (lattice resident in HBM) the line carries `e2e` (the same job
+with the start surface uploaded from pinned host memory and the final one read
+back, per-part times and the bare pinned-copy bandwidth beside it), `roofline`
+(the sweep kernel against the integer-logic pipe, with the HBM view, the
+measured pipe peak and the DRAM traffic of the committed ncu capture),
+`cpu_baseline` / `cpu_all_cores` / `cpu_rsu` (the oracle on a bounded sample),
+`clocks`, `gpu_launches`, and the `batch` (ensemble) and `surrogate` sections.
+
 `--impl reference` times the CPU oracle (the plain single-threaded
 restatement of the same schedule) on a bounded sample of the workload.
 Under torchrun every rank runs its own independent realisation (sample =
