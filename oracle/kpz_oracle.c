@@ -36,11 +36,27 @@
  *     xi = bit b of P[2*(r&1)], yi = bit b of P[2*(r&1)+1]
  *     u = 4cx + 2qx + xi, v = 4cy + 2qy + yi  (tile-local); dead if u==0 or v==0
  *     site (i,j) = ((ox + tx*Bx + u) mod L, (oy + ty*By + v) mod L)
- *   acceptance number of that attempt (16 bits, level 0 = most significant):
- *     A_m = philox(3<<28 | ((cy*nwx+wx)<<6) | (r<<2) | m, T, s, sample), m = 0..3
- *     level n uses bit b of A_{n>>2}[n&3];  U = sum_n bit << (15-n)
- *   a minimum flips iff U < Tp, a maximum flips iff U < Tq,
- *   Tp = min(65536, floor(p*65536 + 0.5)), likewise Tq.
+ *   acceptance (16-bit number U, a minimum flips iff U < Tp, a maximum iff
+ *   U < Tq, Tp = min(65536, floor(p*65536 + 0.5)), likewise Tq). The attempts
+ *   of one round are decided together per row word rw = cy*nwx + wx (the 32
+ *   cells cx = 32 wx + b, b = 0..31, of cell row cy), on the surface before
+ *   the round (attempts of a round never touch each other's sites):
+ *     candidates: cells whose attempted site is live and a local minimum with
+ *       0 < Tp < 65536 or a local maximum with 0 < Tq < 65536 (Tp = 65536
+ *       accepts and Tp = 0 rejects every minimum without a draw; same for q);
+ *     top four bits of U of cell b: bit b of A[0], A[1], A[2], A[3] (most
+ *       significant first), A = philox(3<<28 | rw<<4 | r, T, s, sample);
+ *     a candidate is tied when its top four bits equal those of its threshold
+ *       (bits 15..12); only a tied candidate draws the low twelve bits: the
+ *       k-th tied candidate of the row word (k = 0, 1, ... in increasing b)
+ *       takes the 16-bit half H of a deep block D, low 12 bits of H,
+ *         k < 4:  D = philox(8<<28 | rw<<8 | (r & 14)<<3, T, s, sample),
+ *                 half 4 (r & 1) + k,
+ *         k >= 4: D = philox(8<<28 | rw<<8 | r<<3 | (1 + (k-4)/8), T, s, sample),
+ *                 half (k-4) mod 8,
+ *       half 2i of a block is the low and half 2i+1 the high 16 bits of word i;
+ *     U = top << 12 | low (low = 0 when not tied: U < T is then decided by
+ *       the top bits alone).
  * C = 2 variant (orc_sweep_c2): 2 x 2 cells, 4 rounds, no position draw.
  * Colour-class random-sequential reference (orc_sweep_colour): tags 6 and 7.
  * Tile-set variant (orc_sweep_tilesets): same origin and tiles, no dead border,
@@ -94,7 +110,7 @@ static void philox_at(uint32_t tag_index, uint32_t c1, uint32_t s, uint32_t samp
 }
 
 enum { TAG_ORIGIN = 0, TAG_SET = 1, TAG_POS = 2, TAG_ACC = 3, TAG_RSU = 4, TAG_PHASE = 5,
-       TAG_CLASS = 6, TAG_CACC = 7 };
+       TAG_CLASS = 6, TAG_CACC = 7, TAG_DEEP = 8 };
 
 /* ------------------------------------------------------------------------- */
 /* Model (Sec. 2.1).                                                          */
@@ -184,19 +200,105 @@ static void position_bits(const orc_params* P, memo* m, uint32_t T, uint32_t s,
     *yi = (w[2 * (r & 1u) + 1] >> b) & 1u;
 }
 
-/* 16-bit acceptance number of cell (cx,cy) in round r of tile T, sweep s. */
-static uint32_t acceptance_number(const orc_params* P, memo* m4, uint32_t T, uint32_t s,
-                                  uint32_t cx, uint32_t cy, uint32_t r) {
-    uint32_t nwx = words_per_cell_row(P->Bx);
-    uint32_t row_word = cy * nwx + (cx >> 5);
-    uint32_t b = cx & 31u, U = 0;
-    for (uint32_t n = 0; n < 16; ++n) {
-        uint32_t mi = n >> 2;
-        uint32_t idx = ((uint32_t)TAG_ACC << 28) | (row_word << 6) | (r << 2) | mi;
-        const uint32_t* w = memo_philox(&m4[mi], idx, T, s, P->sample, P->seed);
-        U |= ((w[n & 3u] >> b) & 1u) << (15 - n);
+/* 16-bit half h (0..7) of a Philox block: half 2i = low, 2i+1 = high 16 bits of word i. */
+static uint32_t half16(const uint32_t w[4], uint32_t h) { return (w[h >> 1] >> (16u * (h & 1u))) & 0xffffu; }
+
+/* Acceptance decisions of one round for the 32 cells of row word rw of tile
+ * T, sweep s (header comment): cand_min / cand_max mark the cells whose
+ * attempted site is a live local minimum / maximum. Returns the mask of
+ * accepted attempts; U (32 entries, may be NULL) receives each drawn
+ * candidate's number (top << 12 | low), 0xffffffff for cells without a draw;
+ * *tied (may be NULL) the mask of tied candidates. */
+static uint32_t row_acceptance(const orc_params* P, uint32_t T, uint32_t s, uint32_t r, uint32_t rw,
+                               uint32_t cand_min, uint32_t cand_max, uint32_t* U, uint32_t* tied) {
+    uint32_t draw_min = (P->Tp > 0u && P->Tp < 65536u) ? cand_min : 0u;
+    uint32_t draw_max = (P->Tq > 0u && P->Tq < 65536u) ? cand_max : 0u;
+    uint32_t acc = (P->Tp == 65536u ? cand_min : 0u) | (P->Tq == 65536u ? cand_max : 0u);
+    uint32_t tmask = 0;
+    if (U)
+        for (uint32_t b = 0; b < 32; ++b) U[b] = 0xffffffffu;
+    if (draw_min | draw_max) {
+        uint32_t A[4], D[4], Dx[4];
+        uint32_t k = 0, have_main = 0, ext = 0xffffffffu;
+        philox_at(((uint32_t)TAG_ACC << 28) | (rw << 4) | r, T, s, P->sample, P->seed, A);
+        for (uint32_t b = 0; b < 32; ++b) {
+            if (!(((draw_min | draw_max) >> b) & 1u)) continue;
+            uint32_t thr = ((draw_min >> b) & 1u) ? P->Tp : P->Tq;
+            uint32_t top = 0;
+            for (uint32_t n = 0; n < 4; ++n) top |= ((A[n] >> b) & 1u) << (3 - n);
+            uint32_t u = top << 12;
+            if (top == (thr >> 12)) {        /* tied: draw the low twelve bits */
+                uint32_t H;
+                if (k < 4) {
+                    if (!have_main) {
+                        philox_at(((uint32_t)TAG_DEEP << 28) | (rw << 8) | ((r & 14u) << 3), T, s,
+                                  P->sample, P->seed, D);
+                        have_main = 1;
+                    }
+                    H = half16(D, 4u * (r & 1u) + k);
+                } else {
+                    uint32_t e = (k - 4) / 8;
+                    if (e != ext) {
+                        philox_at(((uint32_t)TAG_DEEP << 28) | (rw << 8) | (r << 3) | (1u + e), T, s,
+                                  P->sample, P->seed, Dx);
+                        ext = e;
+                    }
+                    H = half16(Dx, (k - 4) % 8);
+                }
+                u |= H & 0xfffu;
+                tmask |= 1u << b;
+                ++k;
+            }
+            if (U) U[b] = u;
+            if (u < thr) acc |= 1u << b;
+        }
     }
-    return U;
+    if (tied) *tied = tmask;
+    return acc;
+}
+
+/* Exported for the tests: row_acceptance with the rates given as thresholds. */
+int orc_row_acceptance(uint64_t seed, uint32_t sample, uint32_t Tp, uint32_t Tq, uint32_t T, uint32_t s,
+                       uint32_t r, uint32_t rw, uint32_t cand_min, uint32_t cand_max,
+                       uint32_t* accept, uint32_t* tied, uint32_t* U) {
+    if (Tp > 65536u || Tq > 65536u || r >= 16u || (cand_min & cand_max) || rw >= (1u << 20)) return -1;
+    orc_params P = {0, 0, 0, Tp, Tq, sample, seed, 0};
+    *accept = row_acceptance(&P, T, s, r, rw, cand_min, cand_max, U, tied);
+    return 0;
+}
+
+/* Quadrant set (0..3) active in round r of a tile whose set word is setw0 =
+ * word 0 of philox(1<<28, T, s, sample): two bits per round (Sec. 3.1: one
+ * of the four sets at random each round, with replacement). */
+static uint32_t set_of_round(uint32_t setw0, uint32_t r) { return (setw0 >> (2 * r)) & 3u; }
+
+/* Device layer (Sec. 3): the origin (ox, oy) of sweep s's tile grid, a
+ * uniformly random site: the low bits of words 0 and 1 of
+ * philox(0<<28, 0, s, sample). */
+void orc_origin(uint32_t L, uint64_t seed, uint32_t sample, uint32_t s, uint32_t* ox, uint32_t* oy) {
+    uint32_t w[4];
+    philox_at((uint32_t)TAG_ORIGIN << 28, 0, s, sample, seed, w);
+    *ox = w[0] & (L - 1);
+    *oy = w[1] & (L - 1);
+}
+
+/* Attempted site of cell (cx, cy) of tile T in round r of sweep s (Sec. 3.1):
+ * the round's quadrant set k (0..3), then the tile-local site
+ * (u, v) = (4 cx + 2 (k & 1) + xi, 4 cy + 2 (k >> 1) + yi). For the tests. */
+int orc_attempt_site(uint32_t L, uint32_t Bx, uint32_t By, uint64_t seed, uint32_t sample, uint32_t s,
+                     uint32_t T, uint32_t r, uint32_t cx, uint32_t cy, uint32_t* u, uint32_t* v, uint32_t* k) {
+    if (L < 4 || Bx < 4 || By < 4 || Bx > L || By > L || r >= 16u || cx >= Bx / 4 || cy >= By / 4 ||
+        T >= (L / Bx) * (L / By))
+        return -1;
+    orc_params P = {L, Bx, By, 0, 0, sample, seed, 0};
+    memo m = {0};
+    uint32_t setw[4], xi, yi;
+    philox_at((uint32_t)TAG_SET << 28, T, s, sample, seed, setw);
+    *k = set_of_round(setw[0], r);
+    position_bits(&P, &m, T, s, cx, cy, r, &xi, &yi);
+    *u = 4 * cx + 2 * (*k & 1u) + xi;
+    *v = 4 * cy + 2 * (*k >> 1) + yi;
+    return 0;
 }
 
 /* A fixed pseudo-random permutation used only to reorder independent work
@@ -212,6 +314,55 @@ static void shuffle(uint32_t* a, uint32_t n, uint64_t state) {
     }
 }
 
+/* Per-cell working storage of one tile's round (ncells = Bx*By/16 entries). */
+typedef struct {
+    uint32_t n;
+    uint32_t* order;   /* order in which the moves of a round are made */
+    uint32_t* u;       /* attempted site (tile-local), u = DEAD on the dead border */
+    uint32_t* v;
+    uint8_t* kind;     /* on the surface before the round: 1 minimum, 2 maximum, 0 neither */
+    uint8_t* acc;      /* 1: the attempt is accepted */
+} cell_work;
+
+enum { DEAD = 0xffffffffu };
+
+static void cell_work_free(cell_work* w) {
+    free(w->order); free(w->u); free(w->v); free(w->kind); free(w->acc);
+    memset(w, 0, sizeof *w);
+}
+
+static int cell_work_alloc(cell_work* w, uint32_t ncells) {
+    w->n = ncells;
+    w->order = (uint32_t*)malloc(sizeof(uint32_t) * ncells);
+    w->u = (uint32_t*)malloc(sizeof(uint32_t) * ncells);
+    w->v = (uint32_t*)malloc(sizeof(uint32_t) * ncells);
+    w->kind = (uint8_t*)malloc(ncells);
+    w->acc = (uint8_t*)malloc(ncells);
+    if (!w->order || !w->u || !w->v || !w->kind || !w->acc) { cell_work_free(w); return -1; }
+    return 0;
+}
+
+/* Slope indices of an attempt at tile-local (u, v), u, v >= 1 when windowed:
+ * win: the tile's Bx x By window (stride Bx); else the periodic L x L lattice. */
+static void site_index(const orc_params* P, int win, uint32_t x0, uint32_t y0, uint32_t u, uint32_t v,
+                       size_t* here, size_t* left, size_t* below) {
+    if (win) {
+        *here = (size_t)v * P->Bx + u; *left = *here - 1; *below = *here - P->Bx;
+    } else {
+        uint32_t L = P->L, i = (x0 + u) & (L - 1), j = (y0 + v) & (L - 1);
+        uint32_t im = (i + L - 1) & (L - 1), jm = (j + L - 1) & (L - 1);
+        *here = (size_t)j * L + i; *left = (size_t)j * L + im; *below = (size_t)jm * L + i;
+    }
+}
+
+/* Eq. (rule) pattern of a site: 1 local minimum, 2 local maximum, 0 neither. */
+static int site_kind(const uint8_t* sx, const uint8_t* sy, size_t here, size_t left, size_t below) {
+    int a = sx[left], b = sx[here], c = sy[below], d = sy[here];
+    if (a == 0 && b == 1 && c == 0 && d == 1) return 1;
+    if (a == 1 && b == 0 && c == 1 && d == 0) return 2;
+    return 0;
+}
+
 /* The 16 single-hit rounds of tile T of sweep s (work-group layer, Sec. 3.1).
  * win == NULL: (sx, sy) is the L x L lattice. win != NULL: (sx, sy) hold only
  * this tile's Bx x By window (row-major, stride Bx, local (u, v) = global
@@ -219,13 +370,13 @@ static void shuffle(uint32_t* a, uint32_t n, uint64_t state) {
  * reads and writes sigma_x(u-1, v), sigma_x(u, v), sigma_y(u, v-1),
  * sigma_y(u, v), all inside the window, so a tile evolves from its window
  * alone; *win receives the height change of global site (0, 0) if the tile
- * holds it. cell_order is scratch for Bx*By/16 entries. */
+ * holds it. cw is scratch for Bx*By/16 cells. */
 static void tile_rounds(const orc_params* P, uint32_t s, uint32_t T, uint32_t ox, uint32_t oy,
-                        uint32_t rounds, uint64_t order, uint32_t* cell_order, memo* mpos,
-                        memo* macc, uint8_t* sx, uint8_t* sy, int64_t* win, int64_t* h00) {
+                        uint32_t rounds, uint64_t order, cell_work* cw, memo* mpos,
+                        uint8_t* sx, uint8_t* sy, int64_t* win, int64_t* h00) {
     uint32_t L = P->L, Bx = P->Bx, By = P->By;
     uint32_t ntx = L / Bx;
-    uint32_t ncx = Bx / 4, ncy = By / 4, ncells = ncx * ncy;
+    uint32_t ncx = Bx / 4, ncy = By / 4, ncells = ncx * ncy, nwx = words_per_cell_row(Bx);
     uint32_t tx = T % ntx, ty = T / ntx;
     uint32_t x0 = ox + tx * Bx, y0 = oy + ty * By;
     uint32_t setw[4];
@@ -235,27 +386,51 @@ static void tile_rounds(const orc_params* P, uint32_t s, uint32_t T, uint32_t ox
      * quadrant sets at random (possibly the same as before) and gives every
      * cell one attempt inside its active quadrant. */
     for (uint32_t r = 0; r < rounds; ++r) {
-        uint32_t k = (setw[0] >> (2 * r)) & 3u;
+        uint32_t k = set_of_round(setw[0], r);
         uint32_t qx = k & 1u, qy = k >> 1;
-        shuffle(cell_order, ncells, order >= 2 ? order * 0x9E3779B97F4A7C15ull + T + 1 : 0);
-        if (order == 1)
-            for (uint32_t c = 0; c < ncells; ++c) cell_order[c] = ncells - 1 - c;
-        for (uint32_t c = 0; c < ncells; ++c) {
-            uint32_t cell = cell_order[c];
-            uint32_t cx = cell % ncx, cy = cell / ncx;
-            uint32_t xi, yi;
+
+        /* 1. Each cell's attempted site and its pattern before the round. */
+        for (uint32_t cell = 0; cell < ncells; ++cell) {
+            uint32_t cx = cell % ncx, cy = cell / ncx, xi, yi;
             position_bits(P, mpos, T, s, cx, cy, r, &xi, &yi);
             uint32_t u = 4 * cx + 2 * qx + xi;
             uint32_t v = 4 * cy + 2 * qy + yi;
-            if (!P->live_border && (u == 0 || v == 0)) continue;   /* dead border of the tile */
-            uint32_t i = (x0 + u) & (L - 1), j = (y0 + v) & (L - 1);
-            uint32_t U = acceptance_number(P, macc, T, s, cx, cy, r);
-            int dh;
-            if (win)
-                dh = attempt_at(sx, sy, (size_t)v * Bx + u, (size_t)v * Bx + u - 1,
-                                (size_t)(v - 1) * Bx + u, U < P->Tp, U < P->Tq);
-            else
-                dh = orc_attempt(L, sx, sy, i, j, U < P->Tp, U < P->Tq);
+            cw->acc[cell] = 0;
+            if (!P->live_border && (u == 0 || v == 0)) {   /* dead border of the tile */
+                cw->u[cell] = DEAD; cw->v[cell] = DEAD; cw->kind[cell] = 0;
+                continue;
+            }
+            size_t here, left, below;
+            site_index(P, win != NULL, x0, y0, u, v, &here, &left, &below);
+            cw->u[cell] = u; cw->v[cell] = v;
+            cw->kind[cell] = (uint8_t)site_kind(sx, sy, here, left, below);
+        }
+
+        /* 2. Acceptance, one row word of 32 cells at a time. */
+        for (uint32_t cy = 0; cy < ncy; ++cy)
+            for (uint32_t wx = 0; wx < nwx; ++wx) {
+                uint32_t cmin = 0, cmax = 0;
+                for (uint32_t b = 0; b < 32 && 32 * wx + b < ncx; ++b) {
+                    uint32_t kd = cw->kind[cy * ncx + 32 * wx + b];
+                    if (kd == 1) cmin |= 1u << b;
+                    if (kd == 2) cmax |= 1u << b;
+                }
+                uint32_t acc = row_acceptance(P, T, s, r, cy * nwx + wx, cmin, cmax, NULL, NULL);
+                for (uint32_t b = 0; b < 32 && 32 * wx + b < ncx; ++b)
+                    cw->acc[cy * ncx + 32 * wx + b] = (uint8_t)((acc >> b) & 1u);
+            }
+
+        /* 3. The accepted moves (their sites are never neighbours, so any order). */
+        shuffle(cw->order, ncells, order >= 2 ? order * 0x9E3779B97F4A7C15ull + T + 1 : 0);
+        if (order == 1)
+            for (uint32_t c = 0; c < ncells; ++c) cw->order[c] = ncells - 1 - c;
+        for (uint32_t c = 0; c < ncells; ++c) {
+            uint32_t cell = cw->order[c];
+            if (cw->u[cell] == DEAD || !cw->acc[cell]) continue;
+            size_t here, left, below;
+            site_index(P, win != NULL, x0, y0, cw->u[cell], cw->v[cell], &here, &left, &below);
+            int dh = attempt_at(sx, sy, here, left, below, 1, 1);
+            uint32_t i = (x0 + cw->u[cell]) & (L - 1), j = (y0 + cw->v[cell]) & (L - 1);
             if (dh != 0 && i == 0 && j == 0) {
                 if (h00) *h00 += dh;
                 if (win) *win += dh;
@@ -281,26 +456,24 @@ int orc_sweep(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32_t Tq,
     orc_params P = {L, Bx, By, Tp, Tq, sample, seed, 0};
 
     /* Device layer: the origin of the tile grid moves to a random site each sweep. */
-    uint32_t w[4];
-    philox_at((uint32_t)TAG_ORIGIN << 28, 0, s, sample, seed, w);
-    uint32_t ox = w[0] & (L - 1), oy = w[1] & (L - 1);
+    uint32_t ox, oy;
+    orc_origin(L, seed, sample, s, &ox, &oy);
 
     uint32_t ntx = L / Bx, nty = L / By, ntiles = ntx * nty;
-    uint32_t ncx = Bx / 4, ncy = By / 4, ncells = ncx * ncy;
     uint32_t* tile_order = (uint32_t*)malloc(sizeof(uint32_t) * ntiles);
-    uint32_t* cell_order = (uint32_t*)malloc(sizeof(uint32_t) * ncells);
-    if (!tile_order || !cell_order) { free(tile_order); free(cell_order); return -1; }
+    cell_work cw;
+    if (!tile_order || cell_work_alloc(&cw, (Bx / 4) * (By / 4))) { free(tile_order); return -1; }
     shuffle(tile_order, ntiles, order >= 2 ? order : 0);
     if (order == 1)
         for (uint32_t n = 0; n < ntiles; ++n) tile_order[n] = ntiles - 1 - n;
 
-    memo mpos = {0}, macc[4] = {{0}};
+    memo mpos = {0};
     for (uint32_t n = 0; n < ntiles; ++n) {
         uint32_t T = tile_order[n];
-        tile_rounds(&P, s, T, ox, oy, rounds, order, cell_order, &mpos, macc, sx, sy, NULL, h00);
+        tile_rounds(&P, s, T, ox, oy, rounds, order, &cw, &mpos, sx, sy, NULL, h00);
     }
     free(tile_order);
-    free(cell_order);
+    cell_work_free(&cw);
     return 0;
 }
 
@@ -321,9 +494,8 @@ int orc_sweep_c2(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32_t Tq,
     if (L < 4 || (L & (L - 1)) || Bx < 4 || By < 4 || (Bx & (Bx - 1)) || (By & (By - 1)) ||
         Bx > L || By > L || Tp > 65536u || Tq > 65536u)
         return -1;
-    uint32_t w[4];
-    philox_at((uint32_t)TAG_ORIGIN << 28, 0, s, sample, seed, w);
-    uint32_t ox = w[0] & (L - 1), oy = w[1] & (L - 1);
+    uint32_t ox, oy;
+    orc_origin(L, seed, sample, s, &ox, &oy);
     uint32_t ntx = L / Bx, nty = L / By, ntiles = ntx * nty;
     uint32_t ncx = Bx / 2, ncy = By / 2, ncells = ncx * ncy, nwx = words_per_cell_row(Bx);
     uint32_t* tile_order = (uint32_t*)malloc(sizeof(uint32_t) * ntiles);
@@ -366,40 +538,56 @@ int orc_sweep_c2(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32_t Tq,
     return 0;
 }
 
-/* Tile T of sweep s started from the flat configuration (Sec. 2.1), computed
- * on its own Bx x By window: (sx_win, sy_win) receive the window's slopes after
- * the sweep (row-major, stride Bx, local (u, v) = global ((x0+u) mod L,
- * (y0+v) mod L) with (x0, y0) the tile's anchor), *anchor_x / *anchor_y the
- * anchor, *dh00 the height change of site (0, 0) (0 unless the tile holds it).
- * Exact for a lattice that is flat when sweep s starts (tiles of one sweep do
- * not interact). Returns 0, or -1 on bad input. */
-int orc_flat_tile_sweep(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32_t Tq,
-                        uint64_t seed, uint32_t sample, uint32_t s, uint32_t T,
-                        uint8_t* sx_win, uint8_t* sy_win, uint32_t* anchor_x, uint32_t* anchor_y,
-                        int64_t* dh00) {
+/* Tile T of sweep s computed on its own Bx x By window (tiles of one sweep do
+ * not interact, Sec. 3): on entry (sx_win, sy_win) hold the window's slopes
+ * when sweep s starts (row-major, stride Bx, local (u, v) = global
+ * ((x0+u) mod L, (y0+v) mod L) with (x0, y0) the tile's anchor, which
+ * *anchor_x / *anchor_y receive); on return the slopes after the sweep;
+ * *dh00 the height change of site (0, 0) (0 unless the tile holds it).
+ * With window == 0 the anchor is returned and nothing else is touched.
+ * Returns 0, or -1 on bad input. */
+int orc_window_tile_sweep(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32_t Tq,
+                          uint64_t seed, uint32_t sample, uint32_t s, uint32_t T, int window,
+                          uint8_t* sx_win, uint8_t* sy_win, uint32_t* anchor_x, uint32_t* anchor_y,
+                          int64_t* dh00) {
     if (L < 4 || (L & (L - 1)) || Bx < 4 || By < 4 || (Bx & (Bx - 1)) || (By & (By - 1)) ||
         Bx > L || By > L || Tp > 65536u || Tq > 65536u || T >= (L / Bx) * (L / By))
         return -1;
     orc_params P = {L, Bx, By, Tp, Tq, sample, seed, 0};
-    uint32_t w[4];
-    philox_at((uint32_t)TAG_ORIGIN << 28, 0, s, sample, seed, w);
-    uint32_t ox = w[0] & (L - 1), oy = w[1] & (L - 1);
+    uint32_t ox, oy;
+    orc_origin(L, seed, sample, s, &ox, &oy);
     uint32_t ntx = L / Bx, tx = T % ntx, ty = T / ntx;
-    uint32_t x0 = (ox + tx * Bx) & (L - 1), y0 = (oy + ty * By) & (L - 1);
+    *anchor_x = (ox + tx * Bx) & (L - 1);
+    *anchor_y = (oy + ty * By) & (L - 1);
+    if (!window) return 0;
+    cell_work cw;
+    if (cell_work_alloc(&cw, (Bx / 4) * (By / 4))) return -1;
+    memo mpos = {0};
+    int64_t d = 0;
+    tile_rounds(&P, s, T, ox, oy, 16, 0, &cw, &mpos, sx_win, sy_win, &d, NULL);
+    cell_work_free(&cw);
+    *dh00 = d;
+    return 0;
+}
+
+/* Tile T of sweep s started from the flat configuration (Sec. 2.1): the
+ * window of orc_window_tile_sweep filled with the flat start h = (i+j) & 1
+ * (exact for a lattice that is flat when sweep s starts). */
+int orc_flat_tile_sweep(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32_t Tq,
+                        uint64_t seed, uint32_t sample, uint32_t s, uint32_t T,
+                        uint8_t* sx_win, uint8_t* sy_win, uint32_t* anchor_x, uint32_t* anchor_y,
+                        int64_t* dh00) {
+    uint32_t x0, y0;
+    if (orc_window_tile_sweep(L, Bx, By, Tp, Tq, seed, sample, s, T, 0, sx_win, sy_win, &x0, &y0, dh00))
+        return -1;
     for (uint32_t v = 0; v < By; ++v)
         for (uint32_t u = 0; u < Bx; ++u) {
             uint8_t up = (((x0 + u) + (y0 + v)) & 1u) == 0u;   /* flat start */
             sx_win[(size_t)v * Bx + u] = up;
             sy_win[(size_t)v * Bx + u] = up;
         }
-    uint32_t* cell_order = (uint32_t*)malloc(sizeof(uint32_t) * (Bx / 4) * (By / 4));
-    if (!cell_order) return -1;
-    memo mpos = {0}, macc[4] = {{0}};
-    int64_t d = 0;
-    tile_rounds(&P, s, T, ox, oy, 16, 0, cell_order, &mpos, macc, sx_win, sy_win, &d, NULL);
-    free(cell_order);
-    *anchor_x = x0; *anchor_y = y0; *dh00 = d;
-    return 0;
+    return orc_window_tile_sweep(L, Bx, By, Tp, Tq, seed, sample, s, T, 1, sx_win, sy_win,
+                                 anchor_x, anchor_y, dh00);
 }
 
 /* The same sweep with the tiles spread over nthreads OpenMP threads (natural
@@ -413,23 +601,23 @@ int orc_sweep_threads(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32_
         Bx > L || By > L || Tp > 65536u || Tq > 65536u || nthreads < 1)
         return -1;
     orc_params P = {L, Bx, By, Tp, Tq, sample, seed, 0};
-    uint32_t w[4];
-    philox_at((uint32_t)TAG_ORIGIN << 28, 0, s, sample, seed, w);
-    uint32_t ox = w[0] & (L - 1), oy = w[1] & (L - 1);
+    uint32_t ox, oy;
+    orc_origin(L, seed, sample, s, &ox, &oy);
     int64_t ntiles = (int64_t)(L / Bx) * (L / By);
     uint32_t ncells = (Bx / 4) * (By / 4);
     int64_t dh = 0;
     int bad = 0;
 #pragma omp parallel num_threads(nthreads) reduction(+ : dh) reduction(| : bad)
     {
-        uint32_t* cell_order = (uint32_t*)malloc(sizeof(uint32_t) * ncells);
-        memo mpos = {0}, macc[4] = {{0}};
-        if (!cell_order) bad = 1;
+        cell_work cw;
+        memo mpos = {0};
+        int ok = cell_work_alloc(&cw, ncells) == 0;
+        if (!ok) bad = 1;
 #pragma omp for schedule(dynamic, 16)
         for (int64_t T = 0; T < ntiles; ++T)
-            if (cell_order)
-                tile_rounds(&P, s, (uint32_t)T, ox, oy, 16, 0, cell_order, &mpos, macc, sx, sy, NULL, &dh);
-        free(cell_order);
+            if (ok)
+                tile_rounds(&P, s, (uint32_t)T, ox, oy, 16, 0, &cw, &mpos, sx, sy, NULL, &dh);
+        if (ok) cell_work_free(&cw);
     }
     if (bad) return -1;
     if (h00) *h00 += dh;
@@ -466,28 +654,26 @@ int orc_sweep_tilesets(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32
         2 * Bx > L || 2 * By > L || Tp > 65536u || Tq > 65536u)
         return -1;
     orc_params P = {L, Bx, By, Tp, Tq, sample, seed, 1};
-    uint32_t w[4];
-    philox_at((uint32_t)TAG_ORIGIN << 28, 0, s, sample, seed, w);
-    uint32_t ox = w[0] & (L - 1), oy = w[1] & (L - 1);
+    uint32_t ox, oy;
+    orc_origin(L, seed, sample, s, &ox, &oy);
     uint32_t perm[4];
     orc_tileset_order(s, sample, seed, perm);
     uint32_t ntx = L / Bx, nty = L / By, ntiles = ntx * nty;
-    uint32_t ncells = (Bx / 4) * (By / 4);
     uint32_t* tile_order = (uint32_t*)malloc(sizeof(uint32_t) * ntiles);
-    uint32_t* cell_order = (uint32_t*)malloc(sizeof(uint32_t) * ncells);
-    if (!tile_order || !cell_order) { free(tile_order); free(cell_order); return -1; }
+    cell_work cw;
+    if (!tile_order || cell_work_alloc(&cw, (Bx / 4) * (By / 4))) { free(tile_order); return -1; }
     shuffle(tile_order, ntiles, order >= 2 ? order : 0);
     if (order == 1)
         for (uint32_t n = 0; n < ntiles; ++n) tile_order[n] = ntiles - 1 - n;
-    memo mpos = {0}, macc[4] = {{0}};
+    memo mpos = {0};
     for (uint32_t phase = 0; phase < 4; ++phase)
         for (uint32_t n = 0; n < ntiles; ++n) {
             uint32_t T = tile_order[n], tx = T % ntx, ty = T / ntx;
             if ((tx & 1u) + 2u * (ty & 1u) != perm[phase]) continue;
-            tile_rounds(&P, s, T, ox, oy, 16, order, cell_order, &mpos, macc, sx, sy, NULL, h00);
+            tile_rounds(&P, s, T, ox, oy, 16, order, &cw, &mpos, sx, sy, NULL, h00);
         }
     free(tile_order);
-    free(cell_order);
+    cell_work_free(&cw);
     return 0;
 }
 

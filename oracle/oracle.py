@@ -43,59 +43,80 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = ctypes.CDLL(build())
-            u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
-            u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
-            i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
-            c = ctypes
-            L.orc_philox.argtypes = [u32p, u32p, u32p]
-            L.orc_threshold.argtypes = [c.c_double]
-            L.orc_threshold.restype = c.c_uint32
-            L.orc_init_flat.argtypes = [c.c_uint32, u8p, u8p]
-            L.orc_attempt.argtypes = [c.c_uint32, u8p, u8p, c.c_uint32, c.c_uint32, c.c_int, c.c_int]
-            L.orc_attempt.restype = c.c_int
-            L.orc_sweep.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32,
-                                    c.c_uint64, c.c_uint32, c.c_uint32, u8p, u8p,
-                                    c.POINTER(c.c_int64), c.c_uint64, c.c_uint32]
-            L.orc_sweep.restype = c.c_int
-            L.orc_run.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32,
-                                  c.c_uint64, c.c_uint32, c.c_uint32, c.c_uint32, u8p, u8p,
-                                  c.POINTER(c.c_int64)]
-            L.orc_run.restype = c.c_int
-            L.orc_rsu_run.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint64, c.c_uint32,
-                                      c.c_uint32, c.c_uint32, u8p, u8p, c.POINTER(c.c_int64)]
-            L.orc_rsu_run.restype = c.c_int
-            L.orc_heights.argtypes = [c.c_uint32, u8p, u8p, i64p]
-            L.orc_sums.argtypes = [c.c_uint32, i64p, c.POINTER(c.c_int64),
-                                   c.POINTER(c.c_uint64), c.POINTER(c.c_uint64)]
-            L.orc_w2.argtypes = [c.c_uint64, c.c_int64, c.c_uint64, c.c_uint64]
-            L.orc_w2.restype = c.c_double
-            L.orc_pack.argtypes = [c.c_uint32, u8p, u8p, u32p]
-            L.orc_unpack.argtypes = [c.c_uint32, u32p, u8p, u8p]
-            L.orc_flat_tile_sweep.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32,
-                                              c.c_uint64, c.c_uint32, c.c_uint32, c.c_uint32, u8p, u8p,
-                                              c.POINTER(c.c_uint32), c.POINTER(c.c_uint32),
-                                              c.POINTER(c.c_int64)]
-            L.orc_flat_tile_sweep.restype = c.c_int
-            L.orc_sweep_threads.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32,
-                                            c.c_uint64, c.c_uint32, c.c_uint32, u8p, u8p,
-                                            c.POINTER(c.c_int64), c.c_int]
-            L.orc_sweep_threads.restype = c.c_int
-            L.orc_sweep_tilesets.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32,
-                                             c.c_uint64, c.c_uint32, c.c_uint32, u8p, u8p,
-                                             c.POINTER(c.c_int64), c.c_uint64]
-            L.orc_sweep_tilesets.restype = c.c_int
-            L.orc_tileset_order.argtypes = [c.c_uint32, c.c_uint32, c.c_uint64, u32p]
-            L.orc_tileset_order.restype = c.c_int
-            L.orc_sweep_c2.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32,
-                                       c.c_uint64, c.c_uint32, c.c_uint32, u8p, u8p,
-                                       c.POINTER(c.c_int64), c.c_uint64]
-            L.orc_sweep_c2.restype = c.c_int
-            L.orc_sweep_colour.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint64,
-                                           c.c_uint32, c.c_uint32, u8p, u8p, c.POINTER(c.c_int64)]
-            L.orc_sweep_colour.restype = c.c_int
-            _lib = L
+            _lib = load(build())
     return _lib
+
+
+def load(path: str):
+    """Load a compiled oracle library and declare its functions' signatures."""
+    L = ctypes.CDLL(path)
+    u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
+    u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
+    i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+    c = ctypes
+    L.orc_philox.argtypes = [u32p, u32p, u32p]
+    L.orc_threshold.argtypes = [c.c_double]
+    L.orc_threshold.restype = c.c_uint32
+    L.orc_init_flat.argtypes = [c.c_uint32, u8p, u8p]
+    L.orc_attempt.argtypes = [c.c_uint32, u8p, u8p, c.c_uint32, c.c_uint32, c.c_int, c.c_int]
+    L.orc_attempt.restype = c.c_int
+    L.orc_sweep.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32,
+                            c.c_uint64, c.c_uint32, c.c_uint32, u8p, u8p,
+                            c.POINTER(c.c_int64), c.c_uint64, c.c_uint32]
+    L.orc_sweep.restype = c.c_int
+    L.orc_run.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32,
+                          c.c_uint64, c.c_uint32, c.c_uint32, c.c_uint32, u8p, u8p,
+                          c.POINTER(c.c_int64)]
+    L.orc_run.restype = c.c_int
+    L.orc_rsu_run.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint64, c.c_uint32,
+                              c.c_uint32, c.c_uint32, u8p, u8p, c.POINTER(c.c_int64)]
+    L.orc_rsu_run.restype = c.c_int
+    L.orc_heights.argtypes = [c.c_uint32, u8p, u8p, i64p]
+    L.orc_sums.argtypes = [c.c_uint32, i64p, c.POINTER(c.c_int64),
+                           c.POINTER(c.c_uint64), c.POINTER(c.c_uint64)]
+    L.orc_w2.argtypes = [c.c_uint64, c.c_int64, c.c_uint64, c.c_uint64]
+    L.orc_w2.restype = c.c_double
+    L.orc_pack.argtypes = [c.c_uint32, u8p, u8p, u32p]
+    L.orc_unpack.argtypes = [c.c_uint32, u32p, u8p, u8p]
+    L.orc_flat_tile_sweep.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32,
+                                      c.c_uint64, c.c_uint32, c.c_uint32, c.c_uint32, u8p, u8p,
+                                      c.POINTER(c.c_uint32), c.POINTER(c.c_uint32),
+                                      c.POINTER(c.c_int64)]
+    L.orc_flat_tile_sweep.restype = c.c_int
+    L.orc_window_tile_sweep.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32,
+                                        c.c_uint64, c.c_uint32, c.c_uint32, c.c_uint32, c.c_int,
+                                        u8p, u8p, c.POINTER(c.c_uint32), c.POINTER(c.c_uint32),
+                                        c.POINTER(c.c_int64)]
+    L.orc_window_tile_sweep.restype = c.c_int
+    L.orc_origin.argtypes = [c.c_uint32, c.c_uint64, c.c_uint32, c.c_uint32,
+                             c.POINTER(c.c_uint32), c.POINTER(c.c_uint32)]
+    L.orc_attempt_site.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint64, c.c_uint32,
+                                   c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32,
+                                   c.POINTER(c.c_uint32), c.POINTER(c.c_uint32),
+                                   c.POINTER(c.c_uint32)]
+    L.orc_attempt_site.restype = c.c_int
+    L.orc_row_acceptance.argtypes = [c.c_uint64, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32,
+                                     c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32,
+                                     c.POINTER(c.c_uint32), c.POINTER(c.c_uint32), u32p]
+    L.orc_row_acceptance.restype = c.c_int
+    L.orc_sweep_threads.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32,
+                                    c.c_uint64, c.c_uint32, c.c_uint32, u8p, u8p,
+                                    c.POINTER(c.c_int64), c.c_int]
+    L.orc_sweep_threads.restype = c.c_int
+    L.orc_sweep_tilesets.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32,
+                                     c.c_uint64, c.c_uint32, c.c_uint32, u8p, u8p,
+                                     c.POINTER(c.c_int64), c.c_uint64]
+    L.orc_sweep_tilesets.restype = c.c_int
+    L.orc_tileset_order.argtypes = [c.c_uint32, c.c_uint32, c.c_uint64, u32p]
+    L.orc_tileset_order.restype = c.c_int
+    L.orc_sweep_c2.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32,
+                               c.c_uint64, c.c_uint32, c.c_uint32, u8p, u8p,
+                               c.POINTER(c.c_int64), c.c_uint64]
+    L.orc_sweep_c2.restype = c.c_int
+    L.orc_sweep_colour.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint64,
+                                   c.c_uint32, c.c_uint32, u8p, u8p, c.POINTER(c.c_int64)]
+    L.orc_sweep_colour.restype = c.c_int
+    return L
 
 
 # --------------------------------------------------------------------------- #
@@ -131,6 +152,66 @@ def flat_tile_sweep(L, Bx, By, p, q, seed, sample, s, T):
     if rc:
         raise ValueError("bad arguments")
     return sx.reshape(By, Bx), sy.reshape(By, Bx), (ax.value, ay.value), d.value
+
+
+def window_tile_sweep(L, Bx, By, p, q, seed, sample, s, T, sx, sy):
+    """Tile T of sweep s run on its own window: (sx, sy) of shape (By, Bx)
+    indexed [v, u] = global site ((x0+u) mod L, (y0+v) mod L) hold the
+    window when sweep s starts; returns the window after the sweep and the
+    height change of site (0, 0) (0 unless the tile holds it)."""
+    sx = np.ascontiguousarray(sx, np.uint8).reshape(-1).copy()
+    sy = np.ascontiguousarray(sy, np.uint8).reshape(-1).copy()
+    if sx.size != Bx * By or sy.size != Bx * By:
+        raise ValueError("window shape")
+    ax, ay, d = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_int64()
+    rc = lib().orc_window_tile_sweep(L, Bx, By, threshold(p), threshold(q), seed, sample, s, T, 1, sx, sy,
+                                     ctypes.byref(ax), ctypes.byref(ay), ctypes.byref(d))
+    if rc:
+        raise ValueError("bad arguments")
+    return sx.reshape(By, Bx), sy.reshape(By, Bx), d.value
+
+
+def tile_anchor(L, Bx, By, seed, sample, s, T):
+    """Global site (x0, y0) of tile T's local (0, 0) in sweep s."""
+    dummy = np.zeros(1, np.uint8)
+    ax, ay, d = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_int64()
+    rc = lib().orc_window_tile_sweep(L, Bx, By, 0, 0, seed, sample, s, T, 0, dummy, dummy,
+                                     ctypes.byref(ax), ctypes.byref(ay), ctypes.byref(d))
+    if rc:
+        raise ValueError("bad arguments")
+    return ax.value, ay.value
+
+
+def origin(L, seed, sample, s, _lib=None):
+    """Origin (ox, oy) of sweep s's tile grid (device layer, Sec. 3)."""
+    ox, oy = ctypes.c_uint32(), ctypes.c_uint32()
+    (_lib or lib()).orc_origin(L, seed, sample, s, ctypes.byref(ox), ctypes.byref(oy))
+    return ox.value, oy.value
+
+
+def attempt_site(L, Bx, By, seed, sample, s, T, r, cx, cy, _lib=None):
+    """(u, v, k): tile-local site attempted by cell (cx, cy) of tile T in round
+    r of sweep s, and the round's quadrant set k (Sec. 3.1)."""
+    u, v, k = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    rc = (_lib or lib()).orc_attempt_site(L, Bx, By, seed, sample, s, T, r, cx, cy,
+                                ctypes.byref(u), ctypes.byref(v), ctypes.byref(k))
+    if rc:
+        raise ValueError("bad arguments")
+    return u.value, v.value, k.value
+
+
+def row_acceptance(seed, sample, Tp, Tq, T, s, r, rw, cand_min, cand_max, _lib=None):
+    """Acceptance of one round for the 32 cells of row word rw of tile T:
+    returns (accepted mask, tied mask, U) with U[b] the 16-bit number of
+    candidate b (0xffffffff where no number is drawn). Tp, Tq are thresholds
+    out of 2^16."""
+    acc, tied = ctypes.c_uint32(), ctypes.c_uint32()
+    U = np.zeros(32, np.uint32)
+    rc = (_lib or lib()).orc_row_acceptance(seed, sample, Tp, Tq, T, s, r, rw, cand_min, cand_max,
+                                  ctypes.byref(acc), ctypes.byref(tied), U)
+    if rc:
+        raise ValueError("bad arguments")
+    return acc.value, tied.value, U
 
 
 class State:
