@@ -290,12 +290,13 @@ void kpz_mlp_free(kpz_mlp* m);
 
 /* Exact W^2 of a lattice the caller already holds on the device, without
  * allocating anything. The paper has no counterpart to this call; it exists
- * for callers that cannot call cudaMalloc when they need the width: work
- * being captured into a CUDA graph, processes whose device memory is fully
- * reserved by another framework's caching allocator, or loops that must not
- * allocate after start-up. It computes what kpz_roughness computes.
+ * for callers that cannot call cudaMalloc when they need the width: processes
+ * whose device memory is fully reserved by another framework's caching
+ * allocator, or loops that must not allocate after start-up. It computes what
+ * kpz_roughness computes.
  *   lattice_dev: the lattice in the engine's layout, as returned by
- *                kpz_device_lattice (L*L/8 bytes, read only);
+ *                kpz_device_lattice (L*L/8 bytes, read only), in the memory
+ *                of the current device;
  *   L:           its lateral size, a power of two with 128 <= L <= 131072;
  *   parity:      the parity of the absolute height of site (0,0) of the
  *                surface the lattice started from (0 for the flat start, h00 & 1
@@ -308,8 +309,10 @@ void kpz_mlp_free(kpz_mlp* m);
  * library, held until the process exits. L above 131072 returns KPZ_ERANGE;
  * a null pointer or an L that is not a power of two >= 128 returns
  * KPZ_EINVAL. The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture. All calls share the array, which keeps the last
+ * (cudaGetSymbolAddress) with that device current and keeps it for the rest
+ * of the process; make that first call before any stream capture, and do not
+ * call this function again after a reset of that device (cudaDeviceReset),
+ * which invalidates the kept address. All calls share the array, which keeps the last
  * call's contents; the call clears what must start at zero. Calls that
  * overlap on the GPU (other streams, other host threads) race on the array. */
 kpz_status kpz_roughness_static(const void* lattice_dev, uint32_t L, uint32_t parity,

@@ -1,9 +1,9 @@
 // kpz_noalloc.cu -- exact W^2 of a device-resident lattice with no allocation.
 //
 // Some callers cannot allocate device memory at the moment they need the
-// width: code that runs while a stream is being captured into a CUDA graph,
-// processes whose device memory is fully reserved by another framework's
-// caching allocator, or real-time loops that must not allocate after start-up.
+// width: processes whose device memory is fully reserved by another
+// framework's caching allocator, or real-time loops that must not allocate
+// after start-up.
 // kpz_roughness_static gives them the reduction of kpz_roughness on a lattice
 // they already hold (the pointer kpz_device_lattice returns), with its scratch
 // (column-0 heights and three 64-bit accumulators) in the file-scope array
@@ -40,7 +40,8 @@ extern "C" kpz_status kpz_roughness_static(const void* lattice_dev, uint32_t L, 
   void* base = nullptr;
   {
     // First call on this device (which is current): look up the device
-    // address of the static array once and remember it.
+    // address of the static array once and remember it for the process (a
+    // device reset invalidates it; the header says so).
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_scratch_addr[dev]) {
       void* p = nullptr;

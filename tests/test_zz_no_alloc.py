@@ -2,9 +2,8 @@
 computed without allocating anything.
 
 It serves callers that cannot call cudaMalloc at the time they need W^2 --
-work being captured into a CUDA graph, processes whose device memory is held
-by another framework's allocator, loops that must not allocate after
-start-up. Its scratch lives in one static device array; this test checks,
+processes whose device memory is held by another framework's allocator, loops
+that must not allocate after start-up. Its scratch lives in one static device array; this test checks,
 through the C ABI, that it returns exactly what kpz_roughness returns for the
 same lattice, on two calls in a row (the shared scratch must not carry a
 previous call's sums), that it leaves device memory untouched, and that it
