@@ -67,7 +67,7 @@ __device__ __forceinline__ uint4 philox_sk(uint32_t c0, uint32_t c1, uint32_t c2
 
 // Stream tags of the Philox counter word 0 (tag << 28 | index).
 enum : uint32_t { kTagOrigin = 0u, kTagSet = 1u, kTagPos = 2u, kTagAcc = 3u, kTagPhase = 5u,
-                  kTagClass = 6u, kTagClassAcc = 7u };
+                  kTagClass = 6u, kTagClassAcc = 7u, kTagDeep = 8u };
 
 constexpr uint32_t kTile = 128;      // tile edge in sites (device layer)
 constexpr uint32_t kRounds = 16;     // single-hit rounds per sweep = sites per cell

@@ -56,7 +56,9 @@ __device__ __forceinline__ uint4 draw(const SweepParams& P, const TileCtx& tc, u
 // n>>2, call m at counter word 0 = base | m; base holds the stream's tag). Only cells in needp (selected site is a minimum) and needq (a
 // maximum) need a decision; a cell is decided at the first level where U and
 // T differ, so the warp stops drawing levels once no cell of any lane is still
-// tied. The outcome equals the full 16-level comparison.
+// tied. The outcome equals the full 16-level comparison. Used by the C = 2
+// work-group layer and the colour-class reference; the 4 x 4 single-hit
+// rounds draw only as deep as a tie needs (deep_accept below).
 template <bool kSK>
 __device__ __forceinline__ void acceptance(const SweepParams& P, const TileCtx& tc, uint32_t base,
                                            uint32_t needp, uint32_t needq, uint32_t& AP, uint32_t& AQ) {
@@ -81,6 +83,41 @@ __device__ __forceinline__ void acceptance(const SweepParams& P, const TileCtx& 
   }
   AP = (P.Tp >> 16) ? ~0u : ltp;
   AQ = (P.Tq >> 16) ? ~0u : ltq;
+}
+
+// Low twelve bits of the acceptance numbers of the tied candidates of one
+// cell row in round r (eq. rule): tp / tq mark the minima / maxima whose top
+// four bits equal their threshold's. The k-th tied cell (k = 0, 1, ... in
+// increasing cell index) takes 16-bit half 4 (r & 1) + k of the round pair's
+// deep block D for k < 4, and half (k - 4) mod 8 of overflow block
+// 1 + (k - 4) / 8 of this round otherwise (half 2i = low, 2i + 1 = high 16
+// bits of word i); it is accepted when those twelve bits are below its
+// threshold's. Returns the accepted cells. The loop runs once per tied cell
+// of the lane (about one in sixteen candidates).
+template <bool kSK>
+__device__ __forceinline__ uint32_t deep_accept(const SweepParams& P, const TileCtx& tc, uint32_t rw, uint32_t r,
+                                                uint32_t tp, uint32_t tq, const uint4& D) {
+  const uint32_t wlo = (r & 1u) ? D.z : D.x, whi = (r & 1u) ? D.w : D.y;
+  const uint32_t lp = P.Tp & 0xFFFu, lq = P.Tq & 0xFFFu;
+  uint32_t m = tp | tq, acc = 0u, k = 0u;
+  uint4 X = make_uint4(0u, 0u, 0u, 0u);
+  while (m != 0u) {
+    const uint32_t b = (uint32_t)__ffs(m) - 1u;
+    m &= m - 1u;
+    uint32_t w, j;
+    if (k < 4u) {
+      w = (k & 2u) ? whi : wlo;
+      j = k;
+    } else {
+      j = (k - 4u) & 7u;
+      if (j == 0u) X = draw<kSK>(P, tc, (kTagDeep << 28) | (rw << 8) | (r << 3) | (1u + ((k - 4u) >> 3)));
+      w = (j & 4u) ? ((j & 2u) ? X.w : X.z) : ((j & 2u) ? X.y : X.x);
+    }
+    const uint32_t h = ((j & 1u) ? (w >> 16) : w) & 0xFFFu;
+    acc |= (uint32_t)(h < (((tq >> b) & 1u) ? lq : lp)) << b;
+    ++k;
+  }
+  return acc;
 }
 
 // Selected local minima (fmin) and maxima (fmax) of one single-hit round with
@@ -175,11 +212,17 @@ __device__ __forceinline__ void quad_flips(uint32_t (&T)[CR][4][4], const uint32
 // takes masks and flips in one branch; the general path takes the masks in
 // one branch, decides acceptance for all quadrants with the same code (one
 // copy of the acceptance draws), then flips in a second branch.
+// Acceptance (eq. rule, U < T with U uniform 16-bit): the top four bits of
+// every candidate come bit-sliced from one Philox block per cell row and
+// round; only candidates tied with their threshold there take low bits
+// (deep_accept), from the deep block D of the round pair, drawn by the first
+// round of the pair that has a tie in the warp (haveD).
 template <bool kGeneral, int kPar, bool kTrack, int CR, bool kSK, bool kLive = false>
 __device__ __forceinline__ void one_round(uint32_t (&T)[CR][4][4], const uint32_t (&Xi)[CR],
                                           const uint32_t (&Yi)[CR], const uint32_t (&hx)[CR][4],
                                           const uint32_t (&hy)[4], const SweepParams& P,
-                                          const TileCtx& tc, uint32_t lane, uint32_t r, int& dh) {
+                                          const TileCtx& tc, uint32_t lane, uint32_t r, int& dh,
+                                          uint4 (&D)[CR], bool& haveD) {
   const uint32_t k = (tc.setw >> (2u * r)) & 3u;
   uint32_t fmin[CR][2][2], fmax[CR][2][2];
   if (!kGeneral) {
@@ -201,16 +244,58 @@ __device__ __forceinline__ void one_round(uint32_t (&T)[CR][4][4], const uint32_
     case 2: quad_masks<0, 1, true, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, fmin, fmax); break;
     default: quad_masks<1, 1, true, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, fmin, fmax); break;
   }
+  const bool drawp = P.Tp != 0u && P.Tp < 65536u, drawq = P.Tq != 0u && P.Tq < 65536u;
+  uint32_t AP[CR], AQ[CR], up[CR], uq[CR];
+  uint32_t any = 0u;
 #pragma unroll
   for (int row = 0; row < CR; ++row) {
-    uint32_t AP, AQ;
-    acceptance<kSK>(P, tc, (kTagAcc << 28) | ((CR * lane + row) << 6) | (r << 2),
-                    fmin[row][0][0] | fmin[row][0][1] | fmin[row][1][0] | fmin[row][1][1],
-                    fmax[row][0][0] | fmax[row][0][1] | fmax[row][1][0] | fmax[row][1][1], AP, AQ);
+    AP[row] = (P.Tp >> 16) ? ~0u : 0u;
+    AQ[row] = (P.Tq >> 16) ? ~0u : 0u;
+    up[row] = drawp ? (fmin[row][0][0] | fmin[row][0][1] | fmin[row][1][0] | fmin[row][1][1]) : 0u;
+    uq[row] = drawq ? (fmax[row][0][0] | fmax[row][0][1] | fmax[row][1][0] | fmax[row][1][1]) : 0u;
+    any |= up[row] | uq[row];
+  }
+  if (__any_sync(kFull, any != 0u)) {
+    uint32_t ties = 0u;
+#pragma unroll
+    for (int row = 0; row < CR; ++row) {
+      const uint4 A = draw<kSK>(P, tc, (kTagAcc << 28) | ((CR * lane + row) << 4) | r);
+      const uint32_t w[4] = {A.x, A.y, A.z, A.w};
+      uint32_t ltp = 0u, ltq = 0u;
+#pragma unroll
+      for (uint32_t n = 0; n < 4u; ++n) {   // levels 0..3: bits 15..12 of U and T
+        const uint32_t bp = 0u - ((P.Tp >> (15u - n)) & 1u);
+        const uint32_t bq = 0u - ((P.Tq >> (15u - n)) & 1u);
+        ltp |= up[row] & ~w[n] & bp;
+        up[row] &= ~(w[n] ^ bp);
+        ltq |= uq[row] & ~w[n] & bq;
+        uq[row] &= ~(w[n] ^ bq);
+      }
+      AP[row] |= ltp;
+      AQ[row] |= ltq;
+      ties |= up[row] | uq[row];
+    }
+    if (__any_sync(kFull, ties != 0u)) {
+      if (!haveD) {
+#pragma unroll
+        for (int row = 0; row < CR; ++row)
+          D[row] = draw<kSK>(P, tc, (kTagDeep << 28) | ((CR * lane + row) << 8) | ((r & 14u) << 3));
+        haveD = true;
+      }
+#pragma unroll
+      for (int row = 0; row < CR; ++row) {
+        const uint32_t acc = deep_accept<kSK>(P, tc, CR * lane + row, r, up[row], uq[row], D[row]);
+        AP[row] |= up[row] & acc;
+        AQ[row] |= uq[row] & acc;
+      }
+    }
+  }
+#pragma unroll
+  for (int row = 0; row < CR; ++row) {
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-      for (int dx = 0; dx < 2; ++dx) { fmin[row][dy][dx] &= AP; fmax[row][dy][dx] &= AQ; }
+      for (int dx = 0; dx < 2; ++dx) { fmin[row][dy][dx] &= AP[row]; fmax[row][dy][dx] &= AQ[row]; }
   }
   switch (k) {
     case 0: quad_flips<0, 0, kTrack, CR>(T, fmin, fmax, tc, lane, dh); break;
@@ -234,8 +319,10 @@ __device__ __forceinline__ void tile_rounds(uint32_t (&T)[CR][4][4], const uint3
       const uint4 pos = draw<kSK>(P, tc, (kTagPos << 28) | ((CR * lane + row) << 3) | rp);
       X0[row] = pos.x; Y0[row] = pos.y; X1[row] = pos.z; Y1[row] = pos.w;
     }
-    one_round<kGeneral, kPar, kTrack, CR, kSK, kLive>(T, X0, Y0, hx, hy, P, tc, lane, 2u * rp, dh);
-    one_round<kGeneral, kPar, kTrack, CR, kSK, kLive>(T, X1, Y1, hx, hy, P, tc, lane, 2u * rp + 1u, dh);
+    uint4 D[CR];          // deep acceptance block of the round pair (general rates)
+    bool haveD = false;
+    one_round<kGeneral, kPar, kTrack, CR, kSK, kLive>(T, X0, Y0, hx, hy, P, tc, lane, 2u * rp, dh, D, haveD);
+    one_round<kGeneral, kPar, kTrack, CR, kSK, kLive>(T, X1, Y1, hx, hy, P, tc, lane, 2u * rp + 1u, dh, D, haveD);
   }
 }
 
