@@ -152,8 +152,7 @@ SweepParams sweep_params(const kpz_ctx* c) {
   P.Tp = c->Tp;
   P.Tq = c->Tq;
   P.nlev = c->nlev;
-  P.k0 = (uint32_t)(c->seed & 0xffffffffu);
-  P.k1 = (uint32_t)(c->seed >> 32);
+  set_philox_key(P, c->seed);
   P.sample = c->sample;
   P.h00 = c->h00;
   P.queue = c->queue;

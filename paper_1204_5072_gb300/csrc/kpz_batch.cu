@@ -456,8 +456,7 @@ kpz_status prepare(kpz_batch* b, const std::vector<uint64_t>* cap_T) {
     r.P.Tp = acceptance_threshold(s.p);
     r.P.Tq = acceptance_threshold(s.q);
     r.P.nlev = acceptance_levels(r.P.Tp, r.P.Tq);
-    r.P.k0 = (uint32_t)(s.seed & 0xffffffffu);
-    r.P.k1 = (uint32_t)(s.seed >> 32);
+    set_philox_key(r.P, s.seed);
     r.P.sample = s.sample;
     r.P.h00 = m.h00 + i;
     r.general = !(r.P.Tp == 65536u && r.P.Tq == 0u);

@@ -45,6 +45,12 @@ struct SweepParams {
   uint32_t cell;            // work-group cell edge: 4 (default) or 2 (the C = 2 limit)
 };
 
+// Philox key of a seed: its low and high 32-bit words.
+inline void set_philox_key(SweepParams& P, uint64_t seed) {
+  P.k0 = (uint32_t)(seed & 0xffffffffu);
+  P.k1 = (uint32_t)(seed >> 32);
+}
+
 cudaError_t launch_sweep(const SweepParams& P, uint32_t warps_per_cta, cudaStream_t st);
 cudaError_t launch_advance(uint64_t* t_dev, uint32_t n, cudaStream_t st);
 // One sweep of the tile-set variant of the device layer (kpz_tileset.cu):

@@ -92,30 +92,33 @@ __device__ __forceinline__ void acceptance(const SweepParams& P, const TileCtx& 
 // deep block D for k < 4, and half (k - 4) mod 8 of overflow block
 // 1 + (k - 4) / 8 of this round otherwise (half 2i = low, 2i + 1 = high 16
 // bits of word i); it is accepted when those twelve bits are below its
-// threshold's. Returns the accepted cells. The loop runs once per tied cell
-// of the lane (about one in sixteen candidates).
+// threshold's. Returns the accepted cells. A lane has about one tie in
+// sixteen candidates: the first four are taken without branches, more (a
+// few rounds in a hundred per warp) by a loop that draws the overflow blocks.
 template <bool kSK>
 __device__ __forceinline__ uint32_t deep_accept(const SweepParams& P, const TileCtx& tc, uint32_t rw, uint32_t r,
                                                 uint32_t tp, uint32_t tq, const uint4& D) {
   const uint32_t wlo = (r & 1u) ? D.z : D.x, whi = (r & 1u) ? D.w : D.y;
   const uint32_t lp = P.Tp & 0xFFFu, lq = P.Tq & 0xFFFu;
-  uint32_t m = tp | tq, acc = 0u, k = 0u;
-  uint4 X = make_uint4(0u, 0u, 0u, 0u);
-  while (m != 0u) {
-    const uint32_t b = (uint32_t)__ffs(m) - 1u;
-    m &= m - 1u;
-    uint32_t w, j;
-    if (k < 4u) {
-      w = (k & 2u) ? whi : wlo;
-      j = k;
-    } else {
-      j = (k - 4u) & 7u;
+  const uint32_t h[4] = {wlo & 0xFFFu, (wlo >> 16) & 0xFFFu, whi & 0xFFFu, (whi >> 16) & 0xFFFu};
+  uint32_t m = tp | tq, acc = 0u;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t bit = m & (0u - m);   // the k-th tied cell, 0 if there is none
+    m ^= bit;
+    acc |= (h[k] < ((bit & tq) ? lq : lp)) ? bit : 0u;
+  }
+  if (m != 0u) {
+    uint4 X = make_uint4(0u, 0u, 0u, 0u);
+    for (uint32_t k = 4u; m != 0u; ++k) {
+      const uint32_t bit = m & (0u - m);
+      m ^= bit;
+      const uint32_t j = (k - 4u) & 7u;
       if (j == 0u) X = draw<kSK>(P, tc, (kTagDeep << 28) | (rw << 8) | (r << 3) | (1u + ((k - 4u) >> 3)));
-      w = (j & 4u) ? ((j & 2u) ? X.w : X.z) : ((j & 2u) ? X.y : X.x);
+      const uint32_t w = (j & 4u) ? ((j & 2u) ? X.w : X.z) : ((j & 2u) ? X.y : X.x);
+      const uint32_t hk = ((j & 1u) ? (w >> 16) : w) & 0xFFFu;
+      acc |= (hk < ((bit & tq) ? lq : lp)) ? bit : 0u;
     }
-    const uint32_t h = ((j & 1u) ? (w >> 16) : w) & 0xFFFu;
-    acc |= (uint32_t)(h < (((tq >> b) & 1u) ? lq : lp)) << b;
-    ++k;
   }
   return acc;
 }

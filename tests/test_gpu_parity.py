@@ -128,6 +128,29 @@ def test_execution_knobs_do_not_change_result(eng):
                 assert lat.roughness() == ref[1]
 
 
+@pytest.mark.parametrize("p,q", [(1.0, 0.0), (0.9, 0.1)])
+def test_long_runs_of_tiles_match_oracle(eng, p, q):
+    """Runs of 16 and 32 tiles (the lengths the engine picks from L = 2^16
+    up) and shorter ones at L = 4096, with 1, 4 and 8 warps per CTA, over
+    sweeps 1..4 from the flat start and then 3 more from the rough surface:
+    every schedule equals the oracle bit for bit after each sweep."""
+    L, seed = 4096, 13
+    st = O.State.flat(L)
+    want = []
+    for _ in range(7):
+        st.run_threads(1, TILE, TILE, p, q, seed, 0)
+        want.append((st.packed(), st.sums(), st.h00))
+    for run in (32, 16, 8, 1):
+        for wpc in ((1, 4, 8) if run >= 16 else (4,)):
+            lat = eng.Lattice(L, p, q, seed=seed, run=run, warps_per_cta=wpc)
+            for k, (words, sums, h00) in enumerate(want):
+                lat.run(1)
+                r = lat.roughness()
+                assert np.array_equal(lat.slopes(), words), (p, run, wpc, k + 1)
+                assert ((r["S1"], r["S2"]), r["h00"]) == (sums, h00), (p, run, wpc, k + 1)
+            lat.close()
+
+
 def test_resume_is_bit_exact(eng):
     a = eng.Lattice(512, 0.7, 0.2, seed=4, sample=3)
     a.run(7)
