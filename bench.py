@@ -14,8 +14,14 @@ with the start surface uploaded from pinned host memory and the final one read
 back, per-part times and the bare pinned-copy bandwidth beside it), `roofline`
 (the sweep kernel against the integer-logic pipe, with the HBM view, the
 measured pipe peak and the DRAM traffic of the committed ncu capture),
-`cpu_baseline` / `cpu_all_cores` / `cpu_rsu` (the oracle on a bounded sample),
-`clocks`, `gpu_launches`, and the `batch` (ensemble) and `surrogate` sections.
+`roofline_general` (the same kernel at p = 0.95, q = 0.05, the acceptance
+path), `cpu_baseline` / `cpu_all_cores` / `cpu_rsu` (the oracle on a bounded
+sample), `clocks`, `gpu_launches`, `batch` (the 512-realisation batched
+workload at its 10^5-sweep cap in one persistent launch, with construction-free
+baselines -- one launch per realisation, one launch per sweep -- on a
+stratified subset, per L bucket) and `surrogate` (trained on that batch's own
+curves with one size held out; held-out errors, planned run lengths against
+4 L^1.6, saturation times).
 
 `--impl reference` times the CPU oracle (the plain single-threaded
 restatement of the same schedule) on a bounded sample of the workload.
@@ -55,11 +61,14 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample-mcs", type=int, default=100)
     ap.add_argument("--no-batch", action="store_true")
-    ap.add_argument("--batch-cap", type=int, default=200)
+    ap.add_argument("--batch-cap", type=int, default=100_000)
+    ap.add_argument("--batch-per-bucket", type=int, default=3)
     ap.add_argument("--batch-n", type=int, default=512)
     ap.add_argument("--batch-only", action="store_true",
                     help="profiling aid: run only the batched-ensemble section (no comparisons)")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-general", action="store_true")
+    ap.add_argument("--general-sweeps", type=int, default=100)
     return ap.parse_args()
 
 
@@ -78,6 +87,15 @@ def peaks():
 # 20/64 (Philox xors) + 22/32 (masks, tests, flips, neighbour shifts) + 64/512.
 K_ALG_ALU = 20 / 64 + 22 / 32 + 64 / 512
 ALU_LANES_PER_SM = 64   # integer logic pipe: 16 lanes per SM sub-partition per clock
+# General rates (p, q strictly between 0 and 1) add, per attempt: the maximum
+# test (one more logic op per quadrant site: 4/32) and the acceptance of the
+# candidates (attempted site a local minimum or maximum, density C_CAND in the
+# growth regime at p = 0.95: 0.176 minima + 0.202 maxima on oracle surfaces at
+# L = 512, t = 100..2000), which a bit-serial comparison with the threshold
+# decides with 2 random bits on average, each costing 20/128 Philox xors and
+# 2/32 bit-sliced compare ops.
+C_CAND = 0.378
+K_ALG_ALU_GENERAL = K_ALG_ALU + 4 / 32 + C_CAND * 2 * (20 / 128 + 2 / 32)
 
 
 # Files the sweep kernel is compiled from (their hash ties a profile to the source).
@@ -91,12 +109,12 @@ def sweep_source_sha():
     return hashlib.sha256(src).hexdigest()[:16]
 
 
-def measured_traffic(L):
-    """DRAM bytes per sweep launch from the committed ncu summary, if it was
+def measured_traffic(L, profile="sweep_kernel_L65536.md"):
+    """DRAM bytes per sweep launch from a committed ncu summary, if it was
     taken on this size and on the current kernel source; else None."""
     try:
         sha = sweep_source_sha()
-        txt = open(os.path.join(ROOT, "profiles", "sweep_kernel_L65536.md")).read()
+        txt = open(os.path.join(ROOT, "profiles", profile)).read()
         fields = dict(ln.split(": ", 1) for ln in txt.splitlines() if ": " in ln and ln[:1].isalpha())
         if L == 65536 and fields.get("source_sha256") == sha:
             return float(fields["traffic_bytes_per_launch"])
@@ -288,109 +306,181 @@ def run_reference(a):
 
 
 # --------------------------------------------------------------------------- #
-def batch_bench(eng, cap, seed=1, n_specs=512, compare=True):
-    """Batched ensemble (512 realisations shaped like the batched workload: L =
-    2^{8..13} log-uniform, p ~ U[0.5, 1], q = 1 - p, run length min(4 L^1.6, cap)),
-    one persistent graph launch, against (i) one launch per sweep per realisation
-    (kpz_run, W^2 at the same times) and (ii) one persistent launch per realisation."""
+def _timed(fn):
+    """Wall time of fn() with the device idle on both sides."""
     import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fn()
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0
+
+
+def _per_sweep_run(eng, lat, n, times):
+    """One realisation by one launch per sweep (kpz_run), W^2 at its sample times."""
+    tp = 0
+    for t in times:
+        if t > n:
+            break
+        if t > tp:
+            lat.run(t - tp)
+        lat.roughness()
+        tp = t
+
+
+def batch_bench(eng, cap, seed=1, n_specs=512, per_bucket=3, compare=True):
+    """Batched ensemble: the 512 realisations of the batched workload (L =
+    2^{8..13} log-uniform, p ~ U[0.5, 1], q = 1 - p, run length min(4 L^1.6,
+    cap)) in one persistent graph launch, created and autotuned before the
+    clock. Against it, on a stratified subset (`per_bucket` realisations of
+    each L, the first in seed order), every object also created before the
+    clock: (i) one persistent launch per realisation and (ii) one launch per
+    sweep per realisation, both with W^2 at the same times, each L bucket
+    timed on its own beside the batched launch of the same bucket."""
+    import numpy as np
     specs = [(s.L, s.p, s.q, seed, s.sample, min(s.mcs, cap)) for s in I.ensemble_specs(n_specs, seed=seed)]
     attempts = float(sum(L * L * n for L, _, _, _, _, n in specs))
     t0 = time.perf_counter()
     b = eng.Batch(specs, n_samples=64, autotune=True)
     create_s = time.perf_counter() - t0
-    b.run()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    b.run()
-    torch.cuda.synchronize()
-    batched = time.perf_counter() - t0
+    batched = _timed(b.run)
     times = [int(t) for t in b.times()]
+    curves = b.w2()
     info = b.info()
     b.close()
     n = len(specs)
     out = {"metric": "batched realisations/s", "value": n / batched, "unit": "realisations/s",
-           "attempts_per_s": attempts / batched, "seconds": batched,
+           "attempts_per_s": attempts / batched, "seconds": batched, "attempts": attempts,
            "workload": f"{n} realisations, L=2^(8..13) log-uniform, p~U[0.5,1], q=1-p, "
-                       f"T=min(4 L^1.6, {cap}) MCS, W^2 at the common log-spaced times (seed {seed})",
+                       f"T=min(ceil(4 L^1.6), {cap}) MCS, W^2 at the common log-spaced times (seed {seed})",
            "tuning": {k: info[k] for k in ("run", "warps_per_cta", "ctas_per_sm", "grid", "graph", "tile_y")},
-           "autotune_s": create_s}
+           "create_and_autotune_s": create_s}
+    result = {"specs": specs, "times": np.array(times), "w2": curves}
     if not compare:
-        return out
-    t0 = time.perf_counter()
-    for (L, p, q, sd, smp, n) in specs:
-        lat = eng.Lattice(L, p, q, seed=sd, sample=smp)
-        tp = 0
-        for t in times:
-            if t > n:
-                break
-            if t > tp:
-                lat.run(t - tp)
-            lat.roughness()
-            tp = t
-        lat.close()
-    per_sweep = time.perf_counter() - t0
-    t0 = time.perf_counter()
+        return out, result
+    buckets = {}
     for sp in specs:
-        one = eng.Batch([sp], n_samples=64)
-        one.run()
-        one.close()
-    per_real = time.perf_counter() - t0
-    n = len(specs)
-    out["vs_launch_per_sweep"] = {"value": n / per_sweep, "seconds": per_sweep, "speedup": per_sweep / batched}
-    out["vs_launch_per_realisation"] = {"value": n / per_real, "seconds": per_real,
-                                        "speedup": per_real / batched}
-    return out
+        if len(buckets.setdefault(sp[0], [])) < per_bucket:
+            buckets[sp[0]].append(sp)
+    sub = [sp for L in sorted(buckets) for sp in buckets[L]]
+    rows = {}
+    tot = {"batched": 0.0, "per_realisation": 0.0, "per_sweep": 0.0}
+    bsub = eng.Batch(sub, n_samples=64, autotune=True)
+    t_sub = _timed(bsub.run)
+    bsub.close()
+    for L in sorted(buckets):
+        grp = buckets[L]
+        one_b = eng.Batch(grp, n_samples=64, autotune=True)
+        singles = [eng.Batch([sp], n_samples=64, autotune=True) for sp in grp]
+        lats = [eng.Lattice(sp[0], sp[1], sp[2], seed=sp[3], sample=sp[4]) for sp in grp]
+        tb = _timed(one_b.run)
+        tr = _timed(lambda: [x.run() for x in singles])
+        ts = _timed(lambda: [_per_sweep_run(eng, lat, sp[5], times) for lat, sp in zip(lats, grp)])
+        for x in [one_b, *singles, *lats]:
+            x.close()
+        k = len(grp)
+        rows[f"L{L}"] = {"n": k, "mcs": [sp[5] for sp in grp],
+                         "batched_real_per_s": k / tb, "per_realisation_real_per_s": k / tr,
+                         "per_sweep_real_per_s": k / ts,
+                         "speedup_vs_per_realisation": tr / tb, "speedup_vs_per_sweep": ts / tb}
+        tot["batched"] += tb
+        tot["per_realisation"] += tr
+        tot["per_sweep"] += ts
+    k = len(sub)
+    out["subset"] = {"workload": f"{per_bucket} realisations per L bucket ({k} in all), same specs, "
+                                 f"every Batch/Lattice created (and autotuned) before its clock",
+                     "batched_one_launch": {"value": k / t_sub, "seconds": t_sub},
+                     "vs_launch_per_realisation": {"value": k / tot["per_realisation"],
+                                                   "seconds": tot["per_realisation"],
+                                                   "speedup": tot["per_realisation"] / t_sub},
+                     "vs_launch_per_sweep": {"value": k / tot["per_sweep"], "seconds": tot["per_sweep"],
+                                             "speedup": tot["per_sweep"] / t_sub},
+                     "per_bucket": rows}
+    return out, result
 
 
-def surrogate_bench(eng):
-    """Surrogate trained by the engine's kernels on simulated ensemble means
-    (L in {128, 256}, p in {0.7, 0.8, 0.9, 1.0}, q = 1 - p, 64 realisations each,
-    run length 4 L^1.6); error against fresh 128-realisation ensembles at held-out
-    p in {0.75, 0.95}; planned run lengths 2 t_sat against 4 L^1.6."""
+def surrogate_bench(eng, full, cap, held_L=1024, factor=2.0):
+    """Surrogate trained by the engine's kernels on the batched workload's own
+    W^2 curves (`full`: the 512 realisations just simulated), with every
+    realisation of size held_L left out; its error against fresh simulated
+    ensembles at held-out (L, p) -- including L = held_L, absent from
+    training -- and the run lengths it plans (min(cap, factor t_x)) against
+    the fixed rule min(cap, 4 L^1.6)."""
     import math
     import numpy as np
     from paper_1204_5072_gb300 import surrogate as S
 
     def heur(L):
-        return int(min(math.ceil(4 * L ** 1.6), 100_000))
+        return int(min(math.ceil(4 * L ** 1.6), cap))
 
-    def ens(pairs, seeds, run_len):
-        specs = [(L, p, 1 - p, 100 + k, k, run_len(L, p)) for (L, p) in pairs for k in seeds]
-        b = eng.Batch(specs, n_samples=48)
+    specs, times, w2 = full["specs"], full["times"], full["w2"]
+    keep = [i for i, sp in enumerate(specs) if sp[0] != held_L]
+    t0 = time.perf_counter()
+    sur = S.Surrogate.fit([specs[i] for i in keep], times, w2[keep], epochs=300, batch=128, lr=3e-3, seed=1,
+                          p_bin=0.05)
+    train_s = time.perf_counter() - t0
+    n_train = int(sum(((times > 0) & (times <= specs[i][5])).sum() for i in keep))
+
+    def ens(L, p, n_real, T):
+        b = eng.Batch([(L, p, 1 - p, 77, 9000 + k, T) for k in range(n_real)], n_samples=48)
         b.run()
         t, w = b.times(), b.w2()
         b.close()
-        out = {}
-        for (L, p) in pairs:
-            rows = [i for i, sp in enumerate(specs) if sp[0] == L and sp[1] == p]
-            with warnings.catch_warnings():   # times past every run's end are all-NaN columns
-                warnings.simplefilter("ignore", RuntimeWarning)
-                out[(L, p)] = np.nanmean(w[rows], axis=0)
-        return t, out
+        with warnings.catch_warnings():
+            warnings.simplefilter("ignore", RuntimeWarning)
+            return t, np.nanmean(w, axis=0)
 
-    LS, PT, PH = [128, 256], [0.7, 0.8, 0.9, 1.0], [0.75, 0.95]
+    held = {}
     t0 = time.perf_counter()
-    tr_pairs = [(L, p) for L in LS for p in PT]
-    times, means = ens(tr_pairs, range(64), lambda L, p: heur(L))
+    for L, n_real, T in [(256, 64, heur(256)), (held_L, 24, heur(held_L)), (4096, 6, min(heur(4096), 20_000))]:
+        for p in (0.6, 0.9):
+            t, m = ens(L, p, n_real, T)
+            sel = (t >= 1) & (t <= T) & np.isfinite(m)
+            err = float(np.mean(np.abs(sur.w2(L, t[sel], p, 1 - p) / m[sel] - 1)))
+            held[f"L{L}_p{p}"] = {"mean_rel_error": err, "realisations": n_real, "mcs": T,
+                                  "in_training": L != held_L}
     sim_s = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    sur = S.Surrogate.fit([(L, p, 1 - p, 0, 0, heur(L)) for (L, p) in tr_pairs], times,
-                          np.stack([means[k] for k in tr_pairs]), epochs=400, batch=128, lr=3e-3, seed=1)
-    train_s = time.perf_counter() - t0
-    ho = [(L, p) for L in LS for p in PH]
-    th, hmeans = ens(ho, range(200, 328), lambda L, p: heur(L))
-    errs = {}
-    for (L, p), m in hmeans.items():
-        sel = (th >= 1) & (th <= heur(L)) & np.isfinite(m)
-        errs[f"L{L}_p{p}"] = float(np.mean(np.abs(sur.w2(L, th[sel], p, 1 - p) / m[sel] - 1)))
-    planned = {k: int(min(heur(k[0]), math.ceil(2 * sur.t_sat(k[0], k[1], 1 - k[1], t_max=heur(k[0])))))
-               for k in ho}
-    saved = sum((heur(L) - planned[(L, p)]) * L * L for (L, p) in ho) / sum(heur(L) * L * L for (L, p) in ho)
+    # Run lengths for the batched workload's own specs.
+    planned = sur.plan(specs, factor=factor, cap=cap)
+    fixed_att = sum(L * L * heur(L) for (L, *_r) in specs)
+    plan_att = sum(sp[0] * sp[0] * sp[5] for sp in planned)
+    Ls = [256, 512, 1024, 2048, 4096, 8192]
+    # t_x is searched only inside the trained time range (t <= cap): for the
+    # sizes that do not saturate under the cap the network's value is a lower
+    # bound, and the power law through L = 256 and 512 extrapolates instead.
+    tx, _ = sur.t_x_fit(Ls, 0.75, 0.25, t_max=cap)
+    tx_small, z = sur.t_x_fit([256, 512], 0.75, 0.25, t_max=cap)
+    # Plateau reached by the planned runs (sizes that saturate under the cap).
+    plateau = {}
+    for L in (256, 512):
+        for p in (0.6, 0.9):
+            Tp = int(min(cap, math.ceil(factor * sur.t_sat(L, p, 1 - p, t_max=cap))))
+            runs = {}
+            for tag, T, ns in (("fixed", heur(L), 96), ("planned", Tp, 48)):
+                bb = eng.Batch([(L, p, 1 - p, 78, 9500 + k, T) for k in range(128)], n_samples=ns)
+                bb.run()
+                runs[tag] = (bb.times(), bb.w2())
+                bb.close()
+            tl, wl = runs["fixed"]
+            tp_, wp = runs["planned"]
+            per_real = wl[:, (tl >= 0.5 * heur(L)) & (tl <= heur(L))].mean(axis=1)
+            end_w = wp[:, int(np.searchsorted(tp_, Tp))]
+            ref = float(per_real.mean())
+            plateau[f"L{L}_p{p}"] = {"planned_mcs": Tp, "fixed_mcs": heur(L),
+                                     "end_over_plateau": float(end_w.mean()) / ref,
+                                     "std_error": float(np.sqrt(end_w.var(ddof=1) / 128 +
+                                                                per_real.var(ddof=1) / 128)) / ref}
     sur.close()
-    return {"held_out_mean_rel_error": errs, "max_mean_rel_error": max(errs.values()),
-            "planned_mcs": {f"L{L}_p{p}": v for (L, p), v in planned.items()},
-            "fixed_rule_mcs": {f"L{L}": heur(L) for L in LS}, "sweeps_saved_frac": saved,
+    return {"trained_on": f"{len(keep)} curves of the batched workload ({n_train} (L, t, p) points), "
+                          f"averaged into ensemble means over p bins of 0.05, L={held_L} left out",
+            "held_out": held, "max_mean_rel_error": max(v["mean_rel_error"] for v in held.values()),
+            "planned_attempts_frac_of_fixed_rule": plan_att / fixed_att,
+            "planned_vs_fixed_by_L": {f"L{L}": [int(np.mean([sp[5] for sp in planned if sp[0] == L])), heur(L)]
+                                      for L in Ls},
+            "plateau_check": plateau,
+            "t_x_pred": {f"L{L}": float(v) for L, v in zip(Ls, tx)},
+            "t_x_powerlaw_from_L256_512": {"z": z, "extrapolated": {f"L{L}": float(tx_small[1] * (L / 512) ** z)
+                                                                   for L in Ls[2:]}},
             "train_s": train_s, "simulate_s": sim_s}
 
 
@@ -419,7 +509,7 @@ def main():
     from paper_1204_5072_gb300._lib import launch_count
     if a.batch_only:   # profiling aid: the batched-ensemble section alone
         if rank == 0:
-            print(json.dumps(batch_bench(eng, a.batch_cap, n_specs=a.batch_n, compare=False)), flush=True)
+            print(json.dumps(batch_bench(eng, a.batch_cap, n_specs=a.batch_n, compare=False)[0]), flush=True)
         return
 
     w = I.L65536_2000
@@ -501,6 +591,32 @@ def main():
     except Exception as exc:   # report, do not hide
         roofline["peak_probe"] = {"error": str(exc)}
 
+    # The same kernel at general rates (p = 0.95, q = 0.05: acceptance draws),
+    # the path of the batched workload; CUDA events on the engine's stream.
+    roofline_general = None
+    if not a.no_general:
+        lat_g = eng.Lattice(L, 0.95, 0.05, seed=w.seed, sample=replica_sample(rank))
+        lat_g.run(5)
+        torch.cuda.synchronize()
+        ng = max(10, min(200, a.general_sweeps))
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        lat_g.run(ng)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        per_g = g0.elapsed_time(g1) / 1e3 / ng
+        lat_g.close()
+        ach = K_ALG_ALU_GENERAL * L * L / per_g / 1e12
+        roofline_general = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "Top/s",
+                            "frac": ach / alu_peak,
+                            "traffic": measured_traffic(L, "sweep_kernel_general_L65536.md"),
+                            "kernel": "sweep_kernel (general rates)", "p": 0.95, "q": 0.05,
+                            "alg_ops_per_attempt": K_ALG_ALU_GENERAL, "candidate_density": C_CAND,
+                            "launch_ms": per_g * 1e3, "sweeps_timed": ng, "start": "t = 5 from the flat start",
+                            "attempts_per_s": L * L / per_g,
+                            "hbm": {"achieved": alg_bytes / per_g / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                                    "frac": alg_bytes / per_g / 1e9 / hbm_peak}}
+
     # End to end through the C ABI with host buffers: upload the start state
     # from pinned memory, run the job with W^2 sampling, read the final lattice.
     e2e = None
@@ -565,8 +681,11 @@ def main():
         cpu = cpu_baseline(L, a.cpu_sample_mcs)
         cpu_mt = cpu_all_cores(max(10, a.cpu_sample_mcs // 2))
         cpu_seq = cpu_rsu(max(4, a.cpu_sample_mcs // 10))
-    batch = None if (a.no_batch or world > 1) else batch_bench(eng, a.batch_cap, n_specs=a.batch_n)
-    sur = None if (a.no_surrogate or world > 1) else surrogate_bench(eng)
+    batch = sur = None
+    if not (a.no_batch or world > 1):
+        batch, full = batch_bench(eng, a.batch_cap, n_specs=a.batch_n, per_bucket=a.batch_per_bucket)
+        if not a.no_surrogate:
+            sur = surrogate_bench(eng, full, a.batch_cap)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -574,7 +693,7 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
                 "data": "synthetic (flat checkerboard start, p=1 q=0)",
                 "config": job_config(L, mcs, world),
-                "roofline": roofline, "cpu_baseline": cpu, "cpu_all_cores": cpu_mt, "cpu_rsu": cpu_seq,
+                "roofline": roofline, "roofline_general": roofline_general, "cpu_baseline": cpu, "cpu_all_cores": cpu_mt, "cpu_rsu": cpu_seq,
                 "paper_context": PAPER_CONTEXT, "e2e": e2e,
                 "clocks": clk.summary(), "gpu_launches": launches,
                 "w2_final": rough[-1]["w2"], "batch": batch, "surrogate": sur}

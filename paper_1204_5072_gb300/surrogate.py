@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import ctypes
 import math
+import warnings
 
 import numpy as np
 
@@ -134,8 +135,35 @@ def features(L, t, p, q) -> np.ndarray:
     return f.astype(np.float32)
 
 
+def ensemble_curves(specs, times, w2, p_bin=0.05):
+    """Ensemble means of the realisations' W^2 curves: realisations of one L
+    whose p falls in the same bin of width p_bin are averaged (at every time
+    all of them reached), and the mean curve is placed at their mean (p, q).
+    The network is then fitted to log of the ensemble mean, which is the
+    quantity it is judged on; fitted to single realisations it would learn
+    the mean of log W^2, lower by about half the variance of log W^2 (a few
+    per cent where a realisation's W^2 fluctuates by 20 %). p_bin = 0 keeps
+    every curve as it is (for curves that are ensemble means already)."""
+    groups = {}
+    for k, (L, p, q, _seed, _sample, n) in enumerate(specs):
+        key = (L, int(p // p_bin)) if p_bin > 0 else (L, k)
+        groups.setdefault(key, []).append(k)
+    out_specs, out_w2 = [], []
+    for key in sorted(groups):
+        ks = groups[key]
+        n = min(specs[k][5] for k in ks)
+        with warnings.catch_warnings():   # times past every run's end: all-NaN columns
+            warnings.simplefilter("ignore", RuntimeWarning)
+            m = np.nanmean(np.asarray(w2, np.float64)[ks], axis=0)
+        p = float(np.mean([specs[k][1] for k in ks]))
+        q = float(np.mean([specs[k][2] for k in ks]))
+        out_specs.append((key[0], p, q, 0, 0, n))
+        out_w2.append(m)
+    return out_specs, np.array(out_w2)
+
+
 def curves_to_samples(specs, times, w2):
-    """Training rows from batch results: every (realisation, time > 0) with a W^2."""
+    """Training rows from W^2 curves: every (curve, time > 0) with a W^2."""
     X, Y = [], []
     for (L, p, q, _seed, _sample, n), row in zip(specs, w2):
         for t, w in zip(times, row):
@@ -153,7 +181,12 @@ class Surrogate:
         self.mlp = mlp
 
     @classmethod
-    def fit(cls, specs, times, w2, epochs=300, batch=512, lr=3e-3, seed=0) -> "Surrogate":
+    def fit(cls, specs, times, w2, epochs=300, batch=512, lr=3e-3, seed=0, p_bin=0.0) -> "Surrogate":
+        """Train on the W^2 curves of the realisations `specs` (L, p, q, seed,
+        sample, n) sampled at `times`; with p_bin > 0 realisations are first
+        averaged into ensemble means (ensemble_curves)."""
+        if p_bin > 0:
+            specs, w2 = ensemble_curves(specs, times, w2, p_bin)
         x, y = curves_to_samples(specs, times, w2)
         m = MLP(seed=seed)
         m.train(x, y, epochs=epochs, batch=batch, lr=lr, seed=seed, lr_final=lr / 30)
@@ -178,6 +211,23 @@ class Surrogate:
             T = int(min(cap, math.ceil(factor * self.t_sat(L, p, q, t_max=t_max))))
             out.append((L, p, q, seed, sample, max(T, 1)))
         return out
+
+    def planned_batch(self, specs, factor=2.0, cap=100_000, t_max=1e5, **batch_opts):
+        """The realisations (L, p, q, seed, sample, n) as one persistent batch
+        (kpz_batch_create) with the planned run lengths min(cap, factor t_x)
+        instead of n; the batch queues them longest planned run first, so the
+        realisations the surrogate predicts to be the most expensive start
+        first and short ones fill in behind them. Returns (Batch, planned specs)."""
+        from ._lib import Batch
+        planned = self.plan(specs, factor=factor, cap=cap, t_max=t_max)
+        return Batch(planned, **batch_opts), planned
+
+    def t_x_fit(self, Ls, p, q, t_max=1e5):
+        """Saturation times t_x(L) predicted for the sizes Ls and the exponent
+        z of a power-law fit t_x ~ L^z over them (the KPZ class has z ~ 1.6)."""
+        tx = np.array([self.t_sat(L, p, q, t_max=t_max) for L in Ls])
+        z = float(np.polyfit(np.log(np.asarray(Ls, float)), np.log(tx), 1)[0]) if len(Ls) > 1 else float("nan")
+        return tx, z
 
     def close(self):
         self.mlp.close()
