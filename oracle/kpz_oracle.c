@@ -58,6 +58,7 @@
  *     U = top << 12 | low (low = 0 when not tied: U < T is then decided by
  *       the top bits alone).
  * C = 2 variant (orc_sweep_c2): 2 x 2 cells, 4 rounds, no position draw.
+ * Dead border at both layers (orc_sweep_db2): tags 9, 10, 11.
  * Colour-class random-sequential reference (orc_sweep_colour): tags 6 and 7.
  * Tile-set variant (orc_sweep_tilesets): same origin and tiles, no dead border,
  * the four sets (tx & 1) + 2 (ty & 1) swept in an order drawn from
@@ -110,7 +111,7 @@ static void philox_at(uint32_t tag_index, uint32_t c1, uint32_t s, uint32_t samp
 }
 
 enum { TAG_ORIGIN = 0, TAG_SET = 1, TAG_POS = 2, TAG_ACC = 3, TAG_RSU = 4, TAG_PHASE = 5,
-       TAG_CLASS = 6, TAG_CACC = 7, TAG_DEEP = 8 };
+       TAG_CLASS = 6, TAG_CACC = 7, TAG_DEEP = 8, TAG_DBOFF = 9, TAG_DBSITE = 10, TAG_DBACC = 11 };
 
 /* ------------------------------------------------------------------------- */
 /* Model (Sec. 2.1).                                                          */
@@ -588,6 +589,90 @@ int orc_flat_tile_sweep(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint3
         }
     return orc_window_tile_sweep(L, Bx, By, Tp, Tq, seed, sample, s, T, 1, sx_win, sy_win,
                                  anchor_x, anchor_y, dh00);
+}
+
+/* Dead border at both layers (the paper's earlier KPZ scheme, Sec. 3.1: the
+ * dead-border rule of Sec. 3 applied at the work-group layer as well as at
+ * the device layer). Device layer as in orc_sweep: random origin, Bx x By
+ * tiles, each with a dead low row and column. Work-group layer: 16 rounds per
+ * sweep; in round r the tile is cut into 4 x 4 blocks anchored at the
+ * tile-local offset (dx, dy), wrapping inside the tile; a block's low row and
+ * column are its dead border, and each block makes one attempt at a
+ * uniformly random site of its 3 x 3 live interior. A site is in a block's
+ * interior with probability 9/16 over the offset and then chosen with
+ * probability 1/9, so it has on average one attempt per sweep; attempts of
+ * one round never touch each other's slopes (blocks are separated by their
+ * dead borders, tiles by theirs). Random numbers of tile T, sweep s:
+ *   offsets: S = philox(9<<28, T, s, sample), round r:
+ *            dx = (S[r>>3] >> 4(r&7)) & 3, dy = (S[r>>3] >> (4(r&7) + 2)) & 3;
+ *   block k = ky (Bx/4) + kx in round r:
+ *            w = philox(10<<28 | r<<20 | k>>2, T, s, sample)[k&3],
+ *            n = floor(9 w / 2^32), (i, j) = (1 + n mod 3, 1 + n div 3),
+ *            site u = (dx + 4 kx + i) mod Bx, v = (dy + 4 ky + j) mod By,
+ *            no attempt if u = 0 or v = 0 (the tile's dead border);
+ *   acceptance: U = philox(11<<28 | r<<20 | k>>2, T, s, sample)[k&3] >> 16,
+ *            a minimum flips iff U < Tp, a maximum iff U < Tq.
+ * (n is uniform over 0..8 up to 9 / 2^32.) */
+static void db2_site(uint32_t Bx, uint32_t By, uint64_t seed, uint32_t sample, uint32_t s, uint32_t T,
+                     uint32_t r, uint32_t kx, uint32_t ky, uint32_t* u, uint32_t* v, uint32_t* U) {
+    uint32_t S[4], w[4], a[4];
+    philox_at((uint32_t)TAG_DBOFF << 28, T, s, sample, seed, S);
+    uint32_t dx = (S[r >> 3] >> (4 * (r & 7))) & 3u, dy = (S[r >> 3] >> (4 * (r & 7) + 2)) & 3u;
+    uint32_t k = ky * (Bx / 4) + kx;
+    philox_at(((uint32_t)TAG_DBSITE << 28) | (r << 20) | (k >> 2), T, s, sample, seed, w);
+    philox_at(((uint32_t)TAG_DBACC << 28) | (r << 20) | (k >> 2), T, s, sample, seed, a);
+    uint32_t n = (uint32_t)(((uint64_t)w[k & 3] * 9u) >> 32);
+    *u = (dx + 4 * kx + 1 + n % 3) & (Bx - 1);
+    *v = (dy + 4 * ky + 1 + n / 3) & (By - 1);
+    *U = a[k & 3] >> 16;
+}
+
+/* For the tests: the tile-local site (u, v) block (kx, ky) of tile T attempts
+ * in round r of sweep s, and its acceptance number. Returns 0, or -1. */
+int orc_db2_site(uint32_t L, uint32_t Bx, uint32_t By, uint64_t seed, uint32_t sample, uint32_t s,
+                 uint32_t T, uint32_t r, uint32_t kx, uint32_t ky, uint32_t* u, uint32_t* v, uint32_t* U) {
+    if (L < 4 || Bx < 4 || By < 4 || Bx > L || By > L || (Bx & (Bx - 1)) || (By & (By - 1)) || r >= 16u ||
+        kx >= Bx / 4 || ky >= By / 4 || T >= (L / Bx) * (L / By) || (Bx / 4) * (By / 4) > (1u << 22))
+        return -1;
+    db2_site(Bx, By, seed, sample, s, T, r, kx, ky, u, v, U);
+    return 0;
+}
+
+int orc_sweep_db2(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32_t Tq,
+                  uint64_t seed, uint32_t sample, uint32_t s,
+                  uint8_t* sx, uint8_t* sy, int64_t* h00, uint64_t order) {
+    if (L < 4 || (L & (L - 1)) || Bx < 4 || By < 4 || (Bx & (Bx - 1)) || (By & (By - 1)) ||
+        Bx > L || By > L || Tp > 65536u || Tq > 65536u || (Bx / 4) * (By / 4) > (1u << 22))
+        return -1;
+    uint32_t ox, oy;
+    orc_origin(L, seed, sample, s, &ox, &oy);
+    uint32_t ntx = L / Bx, nty = L / By, ntiles = ntx * nty, nbx = Bx / 4, nblk = nbx * (By / 4);
+    uint32_t* tile_order = (uint32_t*)malloc(sizeof(uint32_t) * ntiles);
+    uint32_t* blk_order = (uint32_t*)malloc(sizeof(uint32_t) * nblk);
+    if (!tile_order || !blk_order) { free(tile_order); free(blk_order); return -1; }
+    shuffle(tile_order, ntiles, order >= 2 ? order : 0);
+    if (order == 1)
+        for (uint32_t n = 0; n < ntiles; ++n) tile_order[n] = ntiles - 1 - n;
+    for (uint32_t n = 0; n < ntiles; ++n) {
+        uint32_t T = tile_order[n], tx = T % ntx, ty = T / ntx;
+        uint32_t x0 = ox + tx * Bx, y0 = oy + ty * By;
+        for (uint32_t r = 0; r < 16; ++r) {
+            shuffle(blk_order, nblk, order >= 2 ? order * 0x9E3779B97F4A7C15ull + T + 1 : 0);
+            if (order == 1)
+                for (uint32_t c = 0; c < nblk; ++c) blk_order[c] = nblk - 1 - c;
+            for (uint32_t c = 0; c < nblk; ++c) {
+                uint32_t k = blk_order[c], u, v, U;
+                db2_site(Bx, By, seed, sample, s, T, r, k % nbx, k / nbx, &u, &v, &U);
+                if (u == 0 || v == 0) continue;   /* the tile's dead border */
+                uint32_t i = (x0 + u) & (L - 1), j = (y0 + v) & (L - 1);
+                int dh = orc_attempt(L, sx, sy, i, j, U < Tp, U < Tq);
+                if (dh != 0 && i == 0 && j == 0 && h00) *h00 += dh;
+            }
+        }
+    }
+    free(tile_order);
+    free(blk_order);
+    return 0;
 }
 
 /* The same sweep with the tiles spread over nthreads OpenMP threads (natural

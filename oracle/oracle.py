@@ -116,6 +116,14 @@ def load(path: str):
     L.orc_sweep_colour.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint64,
                                    c.c_uint32, c.c_uint32, u8p, u8p, c.POINTER(c.c_int64)]
     L.orc_sweep_colour.restype = c.c_int
+    L.orc_sweep_db2.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32,
+                                c.c_uint64, c.c_uint32, c.c_uint32, u8p, u8p,
+                                c.POINTER(c.c_int64), c.c_uint64]
+    L.orc_sweep_db2.restype = c.c_int
+    L.orc_db2_site.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint64, c.c_uint32, c.c_uint32,
+                               c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32,
+                               c.POINTER(c.c_uint32), c.POINTER(c.c_uint32), c.POINTER(c.c_uint32)]
+    L.orc_db2_site.restype = c.c_int
     return L
 
 
@@ -200,6 +208,18 @@ def attempt_site(L, Bx, By, seed, sample, s, T, r, cx, cy, _lib=None):
     return u.value, v.value, k.value
 
 
+def db2_site(L, Bx, By, seed, sample, s, T, r, kx, ky):
+    """(u, v, U): tile-local site attempted by block (kx, ky) of tile T in
+    round r of sweep s under dead borders at both layers, and its 16-bit
+    acceptance number."""
+    u, v, U = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    rc = lib().orc_db2_site(L, Bx, By, seed, sample, s, T, r, kx, ky,
+                            ctypes.byref(u), ctypes.byref(v), ctypes.byref(U))
+    if rc:
+        raise ValueError("bad arguments")
+    return u.value, v.value, U.value
+
+
 def row_acceptance(seed, sample, Tp, Tq, T, s, r, rw, cand_min, cand_max, _lib=None):
     """Acceptance of one round for the 32 cells of row word rw of tile T:
     returns (accepted mask, tied mask, U) with U[b] the 16-bit number of
@@ -279,6 +299,23 @@ class State:
             raise ValueError("invalid oracle parameters")
         self.h00 = h.value
         self.t += 1
+        return self
+
+    def sweep_db2(self, Bx, By, p, q, seed, sample=0, order=0):
+        """One sweep with dead borders at both layers (4 x 4 blocks re-anchored
+        at random each round, one attempt per block in its 3 x 3 interior)."""
+        h = ctypes.c_int64(self.h00)
+        rc = lib().orc_sweep_db2(self.L, Bx, By, threshold(p), threshold(q), seed, sample, self.t,
+                                 self.sx, self.sy, ctypes.byref(h), order)
+        if rc:
+            raise ValueError("invalid oracle parameters")
+        self.h00 = h.value
+        self.t += 1
+        return self
+
+    def run_db2(self, n, Bx, By, p, q, seed, sample=0):
+        for _ in range(n):
+            self.sweep_db2(Bx, By, p, q, seed, sample)
         return self
 
     def run_c2(self, n, Bx, By, p, q, seed, sample=0):
