@@ -87,7 +87,13 @@ typedef struct {
                              2 = no decomposition: the random-sequential
                              reference by colour classes (4 * 2^m sub-steps per
                              sweep, each attempting a random 2^-m subset of one
-                             period-2 sublattice, m = colour_sparsity)        */
+                             period-2 sublattice, m = colour_sparsity);
+                             3 = dead borders at both layers (the paper's
+                             earlier KPZ scheme, Sec. 3.1): the dead-border
+                             tiles of 0, and inside each tile 16 rounds of
+                             4 x 4 blocks anchored at a random offset, each
+                             attempting one random site of its 3 x 3 interior
+                             (Philox tags 9-11). 2 and 3 need 128 x 128 tiles */
     uint32_t cell;        /* work-group layer cell edge (Sec. 3.1): 4 (0 = 4):
                              4 x 4 cells, 2 x 2 quadrant sets, 16 rounds per
                              sweep; or 2: the C = 2 limit, 2 x 2 cells whose

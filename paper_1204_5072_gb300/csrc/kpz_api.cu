@@ -195,8 +195,8 @@ kpz_status kpz_init(kpz_ctx** out, uint32_t L, double p, double q, uint64_t seed
     return KPZ_EINVAL;
   kpz_opts o{};
   if (opts) o = *opts;
-  if (o.decomposition > 2u || (o.decomposition == 1u && ((o.by != 0 && o.by != kTile) || L < 2u * kTile)) ||
-      (o.decomposition == 2u && ((o.by != 0 && o.by != kTile) || (o.cell != 0 && o.cell != 4u))) ||
+  if (o.decomposition > 3u || (o.decomposition == 1u && ((o.by != 0 && o.by != kTile) || L < 2u * kTile)) ||
+      (o.decomposition >= 2u && ((o.by != 0 && o.by != kTile) || (o.cell != 0 && o.cell != 4u))) ||
       o.colour_sparsity > 4u || (o.colour_sparsity != 0 && o.decomposition != 2u))
     return KPZ_EINVAL;
   if ((o.cell != 0 && o.cell != 4u && o.cell != 2u) ||
@@ -296,6 +296,7 @@ kpz_status kpz_run(kpz_ctx* ctx, uint64_t n_mcs) {
       P.s_add = i;
       if (ctx->decomposition == 1u)      KPZ_CUDA(launch_sweep_tilesets(P, ctx->stream));
       else if (ctx->decomposition == 2u) KPZ_CUDA(launch_sweep_colour(P, ctx->colour_m, ctx->stream));
+      else if (ctx->decomposition == 3u) KPZ_CUDA(launch_sweep_db2(P, ctx->stream));
       else                               KPZ_CUDA(launch_sweep(P, ctx->wpc, ctx->stream));
     }
     KPZ_CUDA(launch_advance(ctx->t_dev, chunk, ctx->stream));
@@ -496,7 +497,7 @@ kpz_status kpz_ckpt_load(kpz_ctx** out, const char* path, const kpz_opts* opts) 
   CkptHeader hd{};
   if (fread(&hd, sizeof(hd), 1, in.f) != 1 || memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != 1 ||
       !valid_L(hd.L) || hd.bx != kTile || (hd.by != kTile && hd.by != 2u * kTile) ||
-      acceptance_threshold(hd.p) != hd.Tp || acceptance_threshold(hd.q) != hd.Tq || (hd.decomposition & ~0xF100u) > 2u)
+      acceptance_threshold(hd.p) != hd.Tp || acceptance_threshold(hd.q) != hd.Tq || (hd.decomposition & ~0xF100u) > 3u)
     return KPZ_ECKPT;
   kpz_opts o{};
   if (opts) o = *opts;

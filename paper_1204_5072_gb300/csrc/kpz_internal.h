@@ -56,6 +56,8 @@ cudaError_t launch_advance(uint64_t* t_dev, uint32_t n, cudaStream_t st);
 // One sweep of the tile-set variant of the device layer (kpz_tileset.cu):
 // four launches, one per tile set, in the order drawn for the sweep.
 cudaError_t launch_sweep_tilesets(const SweepParams& P, cudaStream_t st);
+// One sweep with dead borders at both layers (kpz_db2.cu): 128 x 128 tiles.
+cudaError_t launch_sweep_db2(const SweepParams& P, cudaStream_t st);
 // One sweep of the random-sequential reference by colour classes (kpz_colour.cu):
 // 4 * 2^m launches, one per sub-step.
 cudaError_t launch_sweep_colour(const SweepParams& P, uint32_t m, cudaStream_t st);
