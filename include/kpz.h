@@ -124,7 +124,8 @@ size_t kpz_device_bytes(uint32_t L);
 /* Create a lattice and set it to the flat start (Sec. 2.1): heights
  * h(i,j) = (i+j) & 1, so W^2 = 1/4. `init` must be 0 (flat start).
  * Preconditions (KPZ_EINVAL otherwise, checked before any allocation):
- *   L a power of two with 128 <= L <= 131072; 0 <= p, q <= 1 (no NaN);
+ *   L a power of two with 128 <= L <= 262144 (2^18: 8 GiB of lattice at one
+ *   bit per site, kpz_device_bytes(L) in all); 0 <= p, q <= 1 (no NaN);
  *   bx = 128 (or 0), by = 128 or 256 (or 0). p and q are quantised to multiples of 2^-16
  *   (T = min(65536, floor(x*65536 + 0.5))): attempts accept with U < T for a
  *   uniform 16-bit U. `sample` is the realisation index that enters the

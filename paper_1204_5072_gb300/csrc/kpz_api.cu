@@ -65,7 +65,8 @@ constexpr size_t kCkptHostMax = kIoMax;
 
 size_t align_up(size_t n) { return (n + kAlign - 1) / kAlign * kAlign; }
 
-bool valid_L(uint32_t L) { return L >= 128u && L <= 131072u && (L & (L - 1u)) == 0u; }
+// Largest lattice: 2^18 (8 GiB at one bit per site, plus 65 MiB of scratch).
+bool valid_L(uint32_t L) { return L >= 128u && L <= 262144u && (L & (L - 1u)) == 0u; }
 
 struct Layout {
   size_t lat, small, col0, io, total;

@@ -54,3 +54,28 @@ def test_edwards_wilkinson_case_saturates_logarithmically():
     alpha = A.fit_power(Ls, sat)[0] / 2
     assert sat[0] < sat[1]
     assert 0.0 < alpha < 0.2, (alpha, sat)
+
+
+def test_edwards_wilkinson_to_kpz_crossover_in_lambda():
+    """The nonlinearity lambda = 2p/(p+q) - 1 (Sec. 2.1) with p + q = 1:
+    lambda = 0 is the Edwards-Wilkinson class (W^2 ~ ln t in 2+1 dimensions,
+    an effective beta near 0.05 over t in [20, 1100]), lambda = 1 the KPZ
+    class (beta ~ 0.24); in between the growth crosses over from the first to
+    the second, later for smaller lambda, so the effective exponent over a
+    fixed window rises monotonically with lambda (measured at L = 512: 0.062,
+    0.068, 0.096, 0.162, 0.215 for lambda = 0, 0.25, 0.5, 0.75, 1)."""
+    eng = engine()
+    L, T, n = 512, 1100, 16
+    betas = []
+    for lam in (0.0, 0.25, 0.5, 0.75, 1.0):
+        p = (1 + lam) / 2
+        b = eng.Batch([(L, p, 1 - p, 21, k, T) for k in range(n)], n_samples=60, run=4)
+        b.run()
+        t = b.times().astype(np.float64)
+        w = b.w2()
+        b.close()
+        m, e = A.ensemble_mean(w)[:2]
+        betas.append(A.fit_beta(t, m, 20, T, err=e)[0])
+    assert all(b1 < b2 for b1, b2 in zip(betas, betas[1:])), betas
+    assert 0.03 < betas[0] < 0.09 and 0.19 < betas[-1] < 0.26, betas
+    assert betas[2] - betas[0] > 0.015 and betas[-1] - betas[2] > 0.06, betas

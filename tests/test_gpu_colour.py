@@ -41,7 +41,7 @@ def test_colour_reference_checkpoint_and_options(eng, tmp_path):
         st.sweep_colour(0.9, 0.1, 3, 0, m=2)
     _same(b, st, "colour reference after a checkpoint")
     for kw in ({"colour_sparsity": 5, "decomposition": 2}, {"colour_sparsity": 2},
-               {"decomposition": 2, "tile_y": 256}, {"decomposition": 3}):
+               {"decomposition": 2, "tile_y": 256}, {"decomposition": 9}):
         with pytest.raises(KpzError) as e:
             eng.Lattice(256, 1.0, 0.0, **kw)
         assert e.value.status == KPZ_EINVAL

@@ -1,10 +1,11 @@
 """The CUDA engine at the benchmark's full size (L = 2^16) and at the largest
-accepted size, where the oracle cannot follow every site: sampled tiles of
+accepted sizes (2^17, 2^18), where the oracle cannot follow every site: sampled tiles of
 the first sweep against the oracle (tiles of one sweep do not interact, so
 the oracle computes each from the flat start on its own window), a valid
 surface (every row of sigma_x and every column of sigma_y sums to zero,
 Sec. 2.1) and the exact width computed a second, independent way."""
 import hashlib
+import os
 
 import numpy as np
 import pytest
@@ -101,6 +102,35 @@ def test_largest_lattice(eng):
     b.close()
 
 
+def test_largest_lattice_first_sweep_matches_oracle(eng):
+    """L = 2^18 (8 GiB at one bit per site, the largest accepted size): one
+    sweep from the flat start, then every row of sigma_x sums to zero (checked
+    in bands), and sampled tiles plus the height of site (0,0) equal the
+    oracle's window computation of that sweep."""
+    L, Bx, seed = 1 << 18, 128, 5
+    lat = eng.Lattice(L, 1.0, 0.0, seed=seed)
+    lat.run(1)
+    r = lat.roughness()
+    assert r["n"] == L * L and r["t"] == 1 and r["w2"] > 0.25
+    words = lat.slopes()
+    lat.close()
+    w = words.reshape(L, L // 16)
+    for j0 in range(0, L, 8192):
+        assert np.all(_popcount(w[j0:j0 + 8192] & np.uint32(0x55555555)).sum(axis=1, dtype=np.int64) == L // 2)
+    ntx = L // Bx
+    ox, oy = O.origin(L, seed, 0, 0)
+    t00 = (((L - oy) % L) // Bx) * ntx + ((L - ox) % L) // Bx
+    rng = np.random.default_rng(3)
+    dh00 = 0
+    for T in sorted({0, ntx - 1, ntx * ntx - 1, t00} | set(rng.integers(0, ntx * ntx, 8).tolist())):
+        sx, sy, (x0, y0), d = O.flat_tile_sweep(L, Bx, Bx, 1.0, 0.0, seed, 0, 0, T)
+        gx, gy = _window(words, L, x0, y0, Bx, Bx)
+        assert np.array_equal(gx, sx) and np.array_equal(gy, sy), T
+        if T == t00:
+            dh00 = d
+    assert r["h00"] == dh00
+
+
 def _window(words, L, x0, y0, Bx, By):
     """sigma_x, sigma_y bits of the window [v, u] = site ((x0+u) mod L, (y0+v) mod L)
     from the packed exchange format (word j*L/16 + i/16, bits 2(i%16), 2(i%16)+1)."""
@@ -139,37 +169,86 @@ def test_L65536_first_sweep_sampled_tiles_match_oracle(eng, p, q, ty):
     assert r["h00"] == dh00 and r["t"] == 1
 
 
+GOLDEN = {"L4096_P1": "l4096_p1_seed1.txt", "L4096_P095": "l4096_p095_seed1.txt"}
+
+
+def _golden(name):
+    """Records (t, S1, S2, h00, sha256 of the packed slopes) written by
+    tests/golden/make_l4096_goldens.py from the CPU oracle alone."""
+    path = os.path.join(os.path.dirname(__file__), "golden", GOLDEN[name])
+    if not os.path.exists(path):
+        pytest.fail(f"missing oracle records {path}")
+    out = []
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        t, s1, s2, h00, digest = line.split()
+        out.append((int(t), int(s1), int(s2), int(h00), digest))
+    return out
+
+
 @pytest.mark.parametrize("w", ["L4096_P1", "L4096_P095"])
 def test_L4096_ten_thousand_sweeps(eng, w):
-    """The L = 4096, 10^4-sweep workloads (p = 1 and p = 0.95): the first sweep's
-    sampled tiles against the oracle's window computation, then the full run
-    through the W^2 sampling times: a valid surface, the width recomputed on
-    the host, a rerun identical, and W^2 growing as the surface roughens."""
+    """The L = 4096, 10^4-sweep workloads (p = 1 and p = 0.95, seed 1): at
+    every one of the run's W^2 sampling times the packed lattice (SHA-256),
+    the exact height sums S1, S2 and h(0,0) equal the oracle's records, and
+    W^2 equals the value the oracle's sums give."""
     from synth import inputs as I
     W = getattr(I, w)
-    L, Bx = W.L, W.bx
+    L = W.L
+    rec = _golden(w)
+    assert [r[0] for r in rec] == I.sample_times(W.mcs)
     lat = eng.Lattice(L, W.p, W.q, seed=W.seed, sample=W.sample)
-    lat.run(1)
-    words = lat.slopes()
-    for T in (0, 31, 17 * 32 + 5, 32 * 32 - 1, 500):
-        sx, sy, (x0, y0), _ = O.flat_tile_sweep(L, Bx, W.by, W.p, W.q, W.seed, W.sample, 0, T)
-        gx, gy = _window(words, L, x0, y0, Bx, W.by)
-        assert np.array_equal(gx, sx) and np.array_equal(gy, sy), (w, T)
-    w2 = []
-    t0 = 1
-    for t in I.sample_times(W.mcs)[1:]:
-        if t > t0:
-            lat.run(t - t0)
-            t0 = t
-        w2.append(lat.roughness()["w2"])
-    r = lat.roughness()
-    words = lat.slopes()
+    words = np.empty(L * L // 16, np.uint32)
+    for t, s1, s2, h00, digest in rec:
+        r = lat.roughness()
+        if t > r["t"]:
+            lat.run(t - r["t"])
+            r = lat.roughness()
+        lat.slopes_into(words)
+        got = (r["t"], r["S1"], r["S2"], r["h00"], hashlib.sha256(words.data).hexdigest())
+        assert got == (t, s1, s2, h00, digest), (w, t)
+        assert r["w2"] == O.w2_from_sums(L * L, s1, s2)
     _row_col_sums_ok(words, L)
-    assert (r["S1"], r["S2"]) == _w2_host(words, L)
-    assert r["t"] == W.mcs
-    again = eng.Lattice(L, W.p, W.q, seed=W.seed, sample=W.sample).run(W.mcs)
-    assert np.array_equal(again.slopes(), words) and again.roughness()["h00"] == r["h00"]
-    assert w2[-1] > 4 * w2[0] and all(np.isfinite(w2))
+
+
+@pytest.mark.parametrize("p,q,ty", [(1.0, 0.0, 128), (0.95, 0.05, 128), (0.95, 0.05, 256)])
+def test_L65536_later_sweeps_sampled_tiles_match_oracle(eng, p, q, ty):
+    """Sweeps 2 to 4 at L = 2^16 in the benchmark's launch configuration (runs
+    of L/4096 tiles, 4-warp CTAs), each from the rough surface the GPU left:
+    for sampled tiles the oracle runs the sweep on the tile's window taken
+    from the GPU's lattice before the sweep (tiles of one sweep do not
+    interact), and the GPU's window after the sweep and the height change of
+    site (0,0) must equal it."""
+    L, Bx, By, seed, sample = 65536, 128, ty, 3, 1
+    lat = eng.Lattice(L, p, q, seed=seed, sample=sample, tile_y=ty)
+    lat.run(1)
+    ntx, nty = L // Bx, L // By
+    rng = np.random.default_rng(11)
+    before = lat.slopes()
+    h_before = lat.roughness()["h00"]
+    after = np.empty_like(before)
+    for s in (1, 2, 3):
+        lat.run(1)
+        lat.slopes_into(after)
+        r = lat.roughness()
+        assert r["t"] == s + 1
+        ox, oy = O.origin(L, seed, sample, s)
+        t00 = (((L - oy) % L) // By) * ntx + ((L - ox) % L) // Bx
+        tiles = {0, ntx - 1, ntx * nty - 1, t00} | set(rng.integers(0, ntx * nty, 12).tolist())
+        dh00 = 0
+        for T in sorted(tiles):
+            x0, y0 = O.tile_anchor(L, Bx, By, seed, sample, s, T)
+            wx, wy = _window(before, L, x0, y0, Bx, By)
+            sx, sy, d = O.window_tile_sweep(L, Bx, By, p, q, seed, sample, s, T, wx, wy)
+            gx, gy = _window(after, L, x0, y0, Bx, By)
+            assert np.array_equal(gx, sx) and np.array_equal(gy, sy), (p, q, ty, s, T)
+            if T == t00:
+                dh00 = d
+        assert r["h00"] - h_before == dh00, (p, q, ty, s)
+        before, after = after, before
+        h_before = r["h00"]
+    lat.close()
 
 
 def test_full_size_import_export_round_trip(eng):

@@ -40,7 +40,7 @@ def test_tileset_checkpoint_and_options(eng, tmp_path):
     st = O.State.flat(512).run_tilesets(7, TILE, TILE, 0.9, 0.1, 3, 0)
     _same(b, st, "tile sets after a checkpoint")
     assert np.array_equal(a.slopes(), b.slopes())
-    for kw in ({"L": 128}, {"tile_y": 256}, {"decomposition": 4}):
+    for kw in ({"L": 128}, {"tile_y": 256}, {"decomposition": 9}):
         args = {"L": 256, "decomposition": 1}
         args.update(kw)
         with pytest.raises(KpzError) as e:
