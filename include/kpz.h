@@ -93,7 +93,16 @@ typedef struct {
                              tiles of 0, and inside each tile 16 rounds of
                              4 x 4 blocks anchored at a random offset, each
                              attempting one random site of its 3 x 3 interior
-                             (Philox tags 9-11). 2 and 3 need 128 x 128 tiles */
+                             (Philox tags 9-11); 4 = no decomposition:
+                             random-sequential updates equal bit for bit to
+                             making the L^2 attempts of a sweep one at a time
+                             (attempt a at the site drawn from Philox tag 4),
+                             run as rounds of non-neighbouring sites whose
+                             next attempt is the earliest around them; needs
+                             L <= 8192, allocates about 20 L^2 bytes of
+                             scratch itself (not in kpz_device_bytes) and
+                             synchronises the stream every sweep.
+                             2, 3 and 4 need 128 x 128 tiles                   */
     uint32_t cell;        /* work-group layer cell edge (Sec. 3.1): 4 (0 = 4):
                              4 x 4 cells, 2 x 2 quadrant sets, 16 rounds per
                              sweep; or 2: the C = 2 limit, 2 x 2 cells whose

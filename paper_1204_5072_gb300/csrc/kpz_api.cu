@@ -11,6 +11,7 @@
 
 #include "kpz.h"
 #include "kpz_internal.h"
+#include "kpz_rsu.h"
 
 using namespace kpz;
 
@@ -33,6 +34,7 @@ struct kpz_ctx {
   cudaStream_t stream = nullptr;
   bool own_buf = false;
   void* buf = nullptr;
+  void* rsu_scratch = nullptr;         // decomposition 4: per-sweep attempt buckets
   size_t buf_bytes = 0;
   uint32_t* lat = nullptr;             // L*L/32 words (one bit per site)
   uint64_t* t_dev = nullptr;           // sweep counter
@@ -196,7 +198,8 @@ kpz_status kpz_init(kpz_ctx** out, uint32_t L, double p, double q, uint64_t seed
     return KPZ_EINVAL;
   kpz_opts o{};
   if (opts) o = *opts;
-  if (o.decomposition > 3u || (o.decomposition == 1u && ((o.by != 0 && o.by != kTile) || L < 2u * kTile)) ||
+  if (o.decomposition > 4u || (o.decomposition == 1u && ((o.by != 0 && o.by != kTile) || L < 2u * kTile)) ||
+      (o.decomposition == 4u && L > 8192u) ||
       (o.decomposition >= 2u && ((o.by != 0 && o.by != kTile) || (o.cell != 0 && o.cell != 4u))) ||
       o.colour_sparsity > 4u || (o.colour_sparsity != 0 && o.decomposition != 2u))
     return KPZ_EINVAL;
@@ -257,6 +260,15 @@ kpz_status kpz_init(kpz_ctx** out, uint32_t L, double p, double q, uint64_t seed
     ctx->own_buf = true;
     ctx->buf_bytes = y.total;
   }
+  if (ctx->decomposition == 4u) {   // per-sweep attempt buckets of the exact random-sequential sweep
+    cudaError_t e = cudaMalloc(&ctx->rsu_scratch, rsu_scratch_bytes(L));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (ctx->own_buf) cudaFree(ctx->buf);
+      delete ctx;
+      return KPZ_ENOMEM;
+    }
+  }
   char* base = (char*)ctx->buf;
   ctx->lat = (uint32_t*)(base + y.lat);
   ctx->t_dev = (uint64_t*)(base + y.small);
@@ -298,6 +310,7 @@ kpz_status kpz_run(kpz_ctx* ctx, uint64_t n_mcs) {
       if (ctx->decomposition == 1u)      KPZ_CUDA(launch_sweep_tilesets(P, ctx->stream));
       else if (ctx->decomposition == 2u) KPZ_CUDA(launch_sweep_colour(P, ctx->colour_m, ctx->stream));
       else if (ctx->decomposition == 3u) KPZ_CUDA(launch_sweep_db2(P, ctx->stream));
+      else if (ctx->decomposition == 4u) KPZ_CUDA(launch_sweep_rsu(P, ctx->rsu_scratch, ctx->stream));
       else                               KPZ_CUDA(launch_sweep(P, ctx->wpc, ctx->stream));
     }
     KPZ_CUDA(launch_advance(ctx->t_dev, chunk, ctx->stream));
@@ -498,7 +511,7 @@ kpz_status kpz_ckpt_load(kpz_ctx** out, const char* path, const kpz_opts* opts) 
   CkptHeader hd{};
   if (fread(&hd, sizeof(hd), 1, in.f) != 1 || memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != 1 ||
       !valid_L(hd.L) || hd.bx != kTile || (hd.by != kTile && hd.by != 2u * kTile) ||
-      acceptance_threshold(hd.p) != hd.Tp || acceptance_threshold(hd.q) != hd.Tq || (hd.decomposition & ~0xF100u) > 3u)
+      acceptance_threshold(hd.p) != hd.Tp || acceptance_threshold(hd.q) != hd.Tq || (hd.decomposition & ~0xF100u) > 4u)
     return KPZ_ECKPT;
   kpz_opts o{};
   if (opts) o = *opts;
@@ -568,6 +581,10 @@ void kpz_free(kpz_ctx* ctx) {
   if (ctx->own_buf && ctx->buf) {
     cudaStreamSynchronize(ctx->stream);
     cudaFree(ctx->buf);
+  }
+  if (ctx->rsu_scratch) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->rsu_scratch);
   }
   delete ctx;
 }

@@ -37,7 +37,7 @@ def test_exports_every_declared_symbol(lib):
 def test_invalid_arguments_rejected_without_device(lib):
     from paper_1204_5072_gb300._lib import KPZ_EINVAL, kpz_opts
     c = ctypes.c_void_p()
-    bad = [(100, 1.0, 0.0), (64, 1.0, 0.0), (1 << 18, 1.0, 0.0), (256, float("nan"), 0.0),
+    bad = [(100, 1.0, 0.0), (64, 1.0, 0.0), (1 << 19, 1.0, 0.0), (256, float("nan"), 0.0),
            (256, 1.5, 0.0), (256, 1.0, -0.1)]
     for L, p, q in bad:
         assert lib.kpz_init(ctypes.byref(c), L, p, q, 1, 0, 0, None) == KPZ_EINVAL
@@ -50,7 +50,13 @@ def test_invalid_arguments_rejected_without_device(lib):
     o = kpz_opts()
     o.by = 256   # 128 x 256 tiles need L >= 256
     assert lib.kpz_init(ctypes.byref(c), 128, 1.0, 0.0, 1, 0, 0, ctypes.byref(o)) == KPZ_EINVAL
-    assert lib.kpz_device_bytes(100) == 0
+    o = kpz_opts()
+    o.decomposition = 4   # the exact random-sequential reference takes L <= 8192
+    assert lib.kpz_init(ctypes.byref(c), 16384, 1.0, 0.0, 1, 0, 0, ctypes.byref(o)) == KPZ_EINVAL
+    o.decomposition = 5
+    assert lib.kpz_init(ctypes.byref(c), 256, 1.0, 0.0, 1, 0, 0, ctypes.byref(o)) == KPZ_EINVAL
+    assert lib.kpz_device_bytes(100) == 0 and lib.kpz_device_bytes(1 << 19) == 0
+    assert lib.kpz_device_bytes(1 << 18) >= (1 << 36) // 8
     assert lib.kpz_device_bytes(256) >= 256 * 256 // 4
     assert lib.kpz_run(None, 1) == KPZ_EINVAL
     lib.kpz_free(None)
