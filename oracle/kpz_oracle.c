@@ -489,11 +489,12 @@ int orc_sweep(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32_t Tq,
  *   nwx = ceil(Bx/128): A_m = philox(3<<28 | ((c4y*nwx+wx) << 6) | (r << 4)
  *   | (a << 2) | m, T, s, sample), level n from bit (c4x & 31) of
  *   A_{n>>2}[n&3]. Returns 0, or -1 on bad input. */
-int orc_sweep_c2(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32_t Tq,
-                 uint64_t seed, uint32_t sample, uint32_t s,
-                 uint8_t* sx, uint8_t* sy, int64_t* h00, uint64_t order) {
+/* The first `rounds` (<= 4) rounds of that sweep; orc_sweep_c2 runs all four. */
+int orc_sweep_c2_rounds(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32_t Tq,
+                        uint64_t seed, uint32_t sample, uint32_t s,
+                        uint8_t* sx, uint8_t* sy, int64_t* h00, uint64_t order, uint32_t rounds) {
     if (L < 4 || (L & (L - 1)) || Bx < 4 || By < 4 || (Bx & (Bx - 1)) || (By & (By - 1)) ||
-        Bx > L || By > L || Tp > 65536u || Tq > 65536u)
+        Bx > L || By > L || Tp > 65536u || Tq > 65536u || rounds > 4)
         return -1;
     uint32_t ox, oy;
     orc_origin(L, seed, sample, s, &ox, &oy);
@@ -511,7 +512,7 @@ int orc_sweep_c2(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32_t Tq,
         uint32_t x0 = ox + tx * Bx, y0 = oy + ty * By;
         uint32_t setw[4];
         philox_at((uint32_t)TAG_SET << 28, T, s, sample, seed, setw);
-        for (uint32_t r = 0; r < 4; ++r) {
+        for (uint32_t r = 0; r < rounds; ++r) {
             uint32_t k = (setw[0] >> (2 * r)) & 3u;
             shuffle(cell_order, ncells, order >= 2 ? order * 0x9E3779B97F4A7C15ull + T + 1 : 0);
             if (order == 1)
@@ -537,6 +538,12 @@ int orc_sweep_c2(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32_t Tq,
     free(tile_order);
     free(cell_order);
     return 0;
+}
+
+int orc_sweep_c2(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32_t Tq,
+                 uint64_t seed, uint32_t sample, uint32_t s,
+                 uint8_t* sx, uint8_t* sy, int64_t* h00, uint64_t order) {
+    return orc_sweep_c2_rounds(L, Bx, By, Tp, Tq, seed, sample, s, sx, sy, h00, order, 4);
 }
 
 /* Tile T of sweep s computed on its own Bx x By window (tiles of one sweep do
@@ -778,10 +785,11 @@ int orc_sweep_tilesets(uint32_t L, uint32_t Bx, uint32_t By, uint32_t Tp, uint32
  *   acceptance U (16 bits, level 0 most significant), level n from bit c4 of
  *   A_{n>>2}[n&3], A_k = philox(7<<28 | i << 9 | cy << 4 | a << 2 | k, T, s, sample).
  * Needs L >= 128. Returns 0, or -1 on bad input. */
-int orc_sweep_colour(uint32_t L, uint32_t Tp, uint32_t Tq, uint32_t m, uint64_t seed, uint32_t sample,
-                     uint32_t s, uint8_t* sx, uint8_t* sy, int64_t* h00) {
+/* The first `nsub` sub-steps of that sweep (nsub >= 4 * 2^m: all of them). */
+int orc_sweep_colour_steps(uint32_t L, uint32_t Tp, uint32_t Tq, uint32_t m, uint64_t seed, uint32_t sample,
+                           uint32_t s, uint8_t* sx, uint8_t* sy, int64_t* h00, uint32_t nsub) {
     if (L < 128 || (L & (L - 1)) || m > 4 || Tp > 65536u || Tq > 65536u) return -1;
-    const uint32_t B = 128, ntx = L / B, K = 4u << m;
+    const uint32_t B = 128, ntx = L / B, K = nsub < (4u << m) ? nsub : (4u << m);
     memo msel = {0}, macc[4] = {{0}};
     for (uint32_t i = 0; i < K; ++i) {
         uint32_t w[4];
@@ -812,6 +820,11 @@ int orc_sweep_colour(uint32_t L, uint32_t Tp, uint32_t Tq, uint32_t m, uint64_t 
             }
     }
     return 0;
+}
+
+int orc_sweep_colour(uint32_t L, uint32_t Tp, uint32_t Tq, uint32_t m, uint64_t seed, uint32_t sample,
+                     uint32_t s, uint8_t* sx, uint8_t* sy, int64_t* h00) {
+    return orc_sweep_colour_steps(L, Tp, Tq, m, seed, sample, s, sx, sy, h00, 4u << m);
 }
 
 /* n sweeps s = t0 .. t0+n-1 in natural order. */

@@ -116,6 +116,13 @@ def load(path: str):
     L.orc_sweep_colour.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint64,
                                    c.c_uint32, c.c_uint32, u8p, u8p, c.POINTER(c.c_int64)]
     L.orc_sweep_colour.restype = c.c_int
+    L.orc_sweep_c2_rounds.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32,
+                                      c.c_uint64, c.c_uint32, c.c_uint32, u8p, u8p,
+                                      c.POINTER(c.c_int64), c.c_uint64, c.c_uint32]
+    L.orc_sweep_c2_rounds.restype = c.c_int
+    L.orc_sweep_colour_steps.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint64,
+                                         c.c_uint32, c.c_uint32, u8p, u8p, c.POINTER(c.c_int64), c.c_uint32]
+    L.orc_sweep_colour_steps.restype = c.c_int
     L.orc_sweep_db2.argtypes = [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32,
                                 c.c_uint64, c.c_uint32, c.c_uint32, u8p, u8p,
                                 c.POINTER(c.c_int64), c.c_uint64]
@@ -278,23 +285,25 @@ class State:
         self.t += 1
         return self
 
-    def sweep_c2(self, Bx, By, p, q, seed, sample=0, order=0):
-        """One sweep with the C = 2 work-group layer (2 x 2 cells, 4 rounds)."""
+    def sweep_c2(self, Bx, By, p, q, seed, sample=0, order=0, rounds=4):
+        """One sweep with the C = 2 work-group layer (2 x 2 cells, 4 rounds;
+        fewer only for tests that look inside a sweep)."""
         h = ctypes.c_int64(self.h00)
-        rc = lib().orc_sweep_c2(self.L, Bx, By, threshold(p), threshold(q), seed, sample, self.t,
-                                self.sx, self.sy, ctypes.byref(h), order)
+        rc = lib().orc_sweep_c2_rounds(self.L, Bx, By, threshold(p), threshold(q), seed, sample, self.t,
+                                       self.sx, self.sy, ctypes.byref(h), order, rounds)
         if rc:
             raise ValueError("invalid oracle parameters")
         self.h00 = h.value
         self.t += 1
         return self
 
-    def sweep_colour(self, p, q, seed, sample=0, m=3):
+    def sweep_colour(self, p, q, seed, sample=0, m=3, nsub=None):
         """One sweep of random-sequential updates by colour classes (4 * 2^m
-        sub-steps, each a random 2^-m subset of one period-2 sublattice)."""
+        sub-steps, each a random 2^-m subset of one period-2 sublattice; the
+        first nsub only, for tests that look inside a sweep)."""
         h = ctypes.c_int64(self.h00)
-        rc = lib().orc_sweep_colour(self.L, threshold(p), threshold(q), m, seed, sample, self.t,
-                                    self.sx, self.sy, ctypes.byref(h))
+        rc = lib().orc_sweep_colour_steps(self.L, threshold(p), threshold(q), m, seed, sample, self.t,
+                                          self.sx, self.sy, ctypes.byref(h), (4 << m) if nsub is None else nsub)
         if rc:
             raise ValueError("invalid oracle parameters")
         self.h00 = h.value
