@@ -73,7 +73,7 @@ def parse():
 
 
 def peaks():
-    """(HBM GB/s, SM max MHz, source) from the driver-written measurements."""
+    """(HBM GB/s, SM max MHz, source) from the measured peaks in MEASURED_PEAKS.json, else fallback figures."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
