@@ -99,3 +99,14 @@ def test_thresholds():
     assert O.threshold(0.5) == 32768
     assert O.threshold(0.95) == 62259      # floor(0.95 * 65536 + 0.5)
     assert O.threshold(1.0 - 1e-12) == 65536
+
+
+def test_threshold_quantisation_bound():
+    """p is used as T / 2^16 with T = floor(p 2^16 + 1/2): the acceptance
+    probability an attempt actually has differs from p by at most 2^-17
+    (7.6e-6), half a quantum, for every p in [0, 1]."""
+    import numpy as np
+    rng = np.random.default_rng(2)
+    for p in np.concatenate([rng.random(20000), np.linspace(0, 1, 4097), [1e-9, 1 - 1e-9, 2.0 ** -17]]):
+        T = O.threshold(float(p))
+        assert 0 <= T <= 65536 and abs(T / 65536 - p) <= 2.0 ** -17 + 1e-15, (p, T)
