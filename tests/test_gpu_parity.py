@@ -172,6 +172,28 @@ def test_rerun_is_deterministic(eng):
     assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
 
 
+# Thresholds at the edges of the acceptance comparison (T = p 2^16): T = 1 and
+# 65535; T = 0x8000 (a tie with the top four bits never accepts: the low
+# twelve bits of T are 0) and 0x8FFF (a tie accepts unless the low bits are
+# 0xFFF); from the flat start every attempted site is a candidate, so many
+# rows have five or more ties and take the overflow blocks.
+EDGE = [(1 / 65536, 65535 / 65536), (0x8000 / 65536, 0x8FFF / 65536), (0x8FFF / 65536, 0x0001 / 65536),
+        (0x1000 / 65536, 0xF000 / 65536)]
+
+
+@pytest.mark.parametrize("p,q", EDGE)
+def test_threshold_edges_bit_exact(eng, p, q):
+    assert (O.threshold(p), O.threshold(q)) in [(1, 65535), (0x8000, 0x8FFF), (0x8FFF, 1), (0x1000, 0xF000)]
+    for ty in (TILE, 2 * TILE):
+        lat = eng.Lattice(512, p, q, seed=19, sample=2, tile_y=ty)
+        st = O.State.flat(512)
+        for k in range(3):
+            lat.run(1)
+            st.sweep(TILE, ty, p, q, 19, 2)
+            _same(lat, st, f"p={p} q={q} By={ty} after sweep {k + 1}")
+        lat.close()
+
+
 # 128 x 256 tiles (two cell rows per lane): the same schedule with By = 256.
 CASES_TALL = [
     (256, 1.0, 0.0, 1, 0, 6),        # one tile row: the tile wraps onto itself in y
