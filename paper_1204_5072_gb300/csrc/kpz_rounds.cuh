@@ -123,17 +123,13 @@ __device__ __forceinline__ uint32_t deep_accept(const SweepParams& P, const Tile
   return acc;
 }
 
-// Selected local minima (fmin) and maxima (fmax) of one single-hit round with
-// active quadrant (QX, QY), from the state before the round, for every cell
-// row; fmax only with kGeneral. kPar = parity of the tile's site (0,0), or 2:
-// taken at run time from tc.pm (all ones when odd). Xi[r], Yi[r]: position
-// bits of cell row r. Selected sites are never neighbours of each other, so
-// masks taken before any flip equal masks taken site by site.
-template <int QX, int QY, bool kGeneral, int kPar, int CR, bool kLive = false>
-__device__ __forceinline__ void quad_masks(const uint32_t (&T)[CR][4][4], const uint32_t (&Xi)[CR],
-                                           const uint32_t (&Yi)[CR], const uint32_t (&hx)[CR][4],
-                                           const uint32_t (&hy)[4], const TileCtx& tc,
-                                           uint32_t (&fmin)[CR][2][2], uint32_t (&fmax)[CR][2][2]) {
+// Neighbours of the active quadrant (QX, QY) that lie outside the cell (x)
+// or outside the cell row (y): xn[r][d] for quadrant row y0 + d of cell row
+// r, yn[r][d] for quadrant column x0 + d.
+template <int QX, int QY, int CR, bool kLive>
+__device__ __forceinline__ void quad_halo(const uint32_t (&T)[CR][4][4], const uint32_t (&hx)[CR][4],
+                                          const uint32_t (&hy)[4], const TileCtx& tc,
+                                          uint32_t (&xn)[CR][2], uint32_t (&yn)[CR][2]) {
   constexpr int x0 = 2 * QX, y0 = 2 * QY;
   // The one y-neighbour per column that lies in another lane.
   uint32_t ysh[2];
@@ -148,50 +144,77 @@ __device__ __forceinline__ void quad_masks(const uint32_t (&T)[CR][4][4], const 
     ysh[1] = tc.last_lane ? hy[x0 + 1] : d1;
   }
 #pragma unroll
-  for (int row = 0; row < CR; ++row) {
-    uint32_t sel[2][2];  // [dy][dx]: cells whose random site is (x0+dx, y0+dy)
-    sel[0][0] = ~Xi[row] & ~Yi[row];
-    sel[0][1] = Xi[row] & ~Yi[row];
-    sel[1][0] = ~Xi[row] & Yi[row];
-    sel[1][1] = Xi[row] & Yi[row];
-    if (!kLive) {   // dead border: tile column u = 0 and row v = 0
-      if (QX == 0) { sel[0][0] &= ~1u; sel[1][0] &= ~1u; }
-      if (QY == 0 && row == 0) { sel[0][0] &= tc.first_row_ok; sel[0][1] &= tc.first_row_ok; }
-    }
-    uint32_t xn[2], yn[2];  // neighbours outside the cell (x) and outside the cell row (y)
+  for (int row = 0; row < CR; ++row)
 #pragma unroll
     for (int d = 0; d < 2; ++d) {
-      xn[d] = (QX == 0) ? ((T[row][y0 + d][3] << 1) | (kLive ? tc.hxl[y0 + d] : 0u))  // cell c-1, col 3
-                        : __funnelshift_r(T[row][y0 + d][0], hx[row][y0 + d], 1);     // cell c+1, col 0
-      if (QY == 0) yn[d] = (row > 0) ? T[row > 0 ? row - 1 : 0][3][x0 + d] : ysh[d];
-      else         yn[d] = (row < CR - 1) ? T[row < CR - 1 ? row + 1 : 0][0][x0 + d] : ysh[d];
+      xn[row][d] = (QX == 0) ? ((T[row][y0 + d][3] << 1) | (kLive ? tc.hxl[y0 + d] : 0u))  // cell c-1, col 3
+                             : __funnelshift_r(T[row][y0 + d][0], hx[row][y0 + d], 1);     // cell c+1, col 0
+      if (QY == 0) yn[row][d] = (row > 0) ? T[row > 0 ? row - 1 : 0][3][x0 + d] : ysh[d];
+      else         yn[row][d] = (row < CR - 1) ? T[row < CR - 1 ? row + 1 : 0][0][x0 + d] : ysh[d];
     }
+}
+
+// The four neighbours of quadrant site (dx, dy) of cell row r and the bit v
+// that marks a higher neighbour (v = b(s) ^ parity(s)). kPar = parity of the
+// tile's site (0,0), or 2: taken at run time from tc.pm (all ones when odd).
+template <int QX, int QY, int kPar, int CR>
+struct SiteView {
+  uint32_t s, nL, nR, nU, nD, v;
+  __device__ __forceinline__ SiteView(const uint32_t (&T)[CR][4][4], const uint32_t (&xn)[CR][2],
+                                      const uint32_t (&yn)[CR][2], const TileCtx& tc, int row, int dx,
+                                      int dy) {
+    const int xp = 2 * QX + dx, yp = 2 * QY + dy;
+    s = T[row][yp][xp];
+    nL = (xp > 0) ? T[row][yp][xp > 0 ? xp - 1 : 0] : xn[row][dy];
+    nR = (xp < 3) ? T[row][yp][xp < 3 ? xp + 1 : 3] : xn[row][dy];
+    nU = (yp > 0) ? T[row][yp > 0 ? yp - 1 : 0][xp] : yn[row][dx];
+    nD = (yp < 3) ? T[row][yp < 3 ? yp + 1 : 3][xp] : yn[row][dx];
+    if (kPar == 2) v = s ^ (((xp + yp) & 1) ? ~tc.pm : tc.pm);
+    else           v = ((kPar + xp + yp) & 1) ? ~s : s;
+  }
+};
+
+// Cells whose random site (Xi, Yi) is quadrant site (dx, dy), without the
+// dead border (tile column u = 0 and row v = 0) unless kLive.
+template <int QX, int QY, bool kLive>
+__device__ __forceinline__ uint32_t selected(uint32_t Xi, uint32_t Yi, const TileCtx& tc, int row, int dx, int dy) {
+  uint32_t sel = (dx ? Xi : ~Xi) & (dy ? Yi : ~Yi);
+  if (!kLive) {
+    if (QX == 0 && dx == 0) sel &= ~1u;
+    if (QY == 0 && dy == 0 && row == 0) sel &= tc.first_row_ok;
+  }
+  return sel;
+}
+
+// Selected local minima (fmin) of one single-hit round with active quadrant
+// (QX, QY), from the state before the round, for every cell row (the
+// p = 1, q = 0 path). Xi[r], Yi[r]: position bits of cell row r. Selected
+// sites are never neighbours of each other, so masks taken before any flip
+// equal masks taken site by site.
+template <int QX, int QY, int kPar, int CR, bool kLive = false>
+__device__ __forceinline__ void quad_masks(const uint32_t (&T)[CR][4][4], const uint32_t (&Xi)[CR],
+                                           const uint32_t (&Yi)[CR], const uint32_t (&hx)[CR][4],
+                                           const uint32_t (&hy)[4], const TileCtx& tc,
+                                           uint32_t (&fmin)[CR][2][2]) {
+  uint32_t xn[CR][2], yn[CR][2];
+  quad_halo<QX, QY, CR, kLive>(T, hx, hy, tc, xn, yn);
+#pragma unroll
+  for (int row = 0; row < CR; ++row)
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
       for (int dx = 0; dx < 2; ++dx) {
-        const int xp = x0 + dx, yp = y0 + dy;
-        const uint32_t s = T[row][yp][xp];
-        const uint32_t nL = (xp > 0) ? T[row][yp][xp > 0 ? xp - 1 : 0] : xn[dy];
-        const uint32_t nR = (xp < 3) ? T[row][yp][xp < 3 ? xp + 1 : 3] : xn[dy];
-        const uint32_t nU = (yp > 0) ? T[row][yp > 0 ? yp - 1 : 0][xp] : yn[dx];
-        const uint32_t nD = (yp < 3) ? T[row][yp < 3 ? yp + 1 : 3][xp] : yn[dx];
-        uint32_t v;   // bit of a higher neighbour
-        if (kPar == 2) v = s ^ (((xp + yp) & 1) ? ~tc.pm : tc.pm);
-        else           v = ((kPar + xp + yp) & 1) ? ~s : s;
-        const uint32_t hL = ~(nL ^ v), hR = ~(nR ^ v), hU = ~(nU ^ v), hD = ~(nD ^ v);
-        fmin[row][dy][dx] = sel[dy][dx] & hL & hR & hU & hD;                       // local minimum
-        fmax[row][dy][dx] = kGeneral ? (sel[dy][dx] & ~hL & ~hR & ~hU & ~hD) : 0u;  // local maximum
+        const SiteView<QX, QY, kPar, CR> n(T, xn, yn, tc, row, dx, dy);
+        fmin[row][dy][dx] = selected<QX, QY, kLive>(Xi[row], Yi[row], tc, row, dx, dy) &
+                            ~(n.nL ^ n.v) & ~(n.nR ^ n.v) & ~(n.nU ^ n.v) & ~(n.nD ^ n.v);
       }
-  }
 }
 
-// Apply the accepted moves of a round with active quadrant (QX, QY): count
-// those of site (0,0) when the tile holds it, then toggle the bits.
+// Apply the moves of a p = 1, q = 0 round with active quadrant (QX, QY):
+// count those of site (0,0) when the tile holds it, then toggle the bits.
 template <int QX, int QY, bool kTrack, int CR>
 __device__ __forceinline__ void quad_flips(uint32_t (&T)[CR][4][4], const uint32_t (&fmin)[CR][2][2],
-                                           const uint32_t (&fmax)[CR][2][2], const TileCtx& tc,
-                                           uint32_t lane, int& dh) {
+                                           const TileCtx& tc, uint32_t lane, int& dh) {
   constexpr int x0 = 2 * QX, y0 = 2 * QY;
 #pragma unroll
   for (int row = 0; row < CR; ++row) {
@@ -201,19 +224,76 @@ __device__ __forceinline__ void quad_flips(uint32_t (&T)[CR][4][4], const uint32
 #pragma unroll
         for (int dx = 0; dx < 2; ++dx)
           if ((uint32_t)(x0 + dx) == tc.xo && (uint32_t)(y0 + dy) == tc.yo)
-            dh += 2 * (int)((fmin[row][dy][dx] >> tc.co) & 1u) - 2 * (int)((fmax[row][dy][dx] >> tc.co) & 1u);
+            dh += 2 * (int)((fmin[row][dy][dx] >> tc.co) & 1u);
     }
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-      for (int dx = 0; dx < 2; ++dx) T[row][y0 + dy][x0 + dx] ^= fmin[row][dy][dx] | fmax[row][dy][dx];
+      for (int dx = 0; dx < 2; ++dx) T[row][y0 + dy][x0 + dx] ^= fmin[row][dy][dx];
+  }
+}
+
+// Candidates of one general-rate round with active quadrant (QX, QY): the
+// selected sites whose four neighbours are all higher (a local minimum) or
+// all lower (a local maximum) -- all four neighbour bits equal, which does
+// not depend on v. Per cell row, upc marks the cells whose candidate is a
+// minimum, uqc those whose candidate is a maximum (a cell has at most one).
+template <int QX, int QY, int kPar, int CR, bool kLive = false>
+__device__ __forceinline__ void quad_cands(const uint32_t (&T)[CR][4][4], const uint32_t (&Xi)[CR],
+                                           const uint32_t (&Yi)[CR], const uint32_t (&hx)[CR][4],
+                                           const uint32_t (&hy)[4], const TileCtx& tc,
+                                           uint32_t (&cand)[CR][2][2], uint32_t (&upc)[CR], uint32_t (&uqc)[CR]) {
+  uint32_t xn[CR][2], yn[CR][2];
+  quad_halo<QX, QY, CR, kLive>(T, hx, hy, tc, xn, yn);
+#pragma unroll
+  for (int row = 0; row < CR; ++row) {
+    uint32_t mn = 0u, any = 0u;
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx) {
+        const SiteView<QX, QY, kPar, CR> n(T, xn, yn, tc, row, dx, dy);
+        const uint32_t c = selected<QX, QY, kLive>(Xi[row], Yi[row], tc, row, dx, dy) &
+                           ~(n.nL ^ n.nR) & ~(n.nU ^ n.nD) & ~(n.nL ^ n.nU);
+        cand[row][dy][dx] = c;
+        mn |= c & ~(n.nL ^ n.v);
+        any |= c;
+      }
+    upc[row] = mn;
+    uqc[row] = any & ~mn;
+  }
+}
+
+// Apply the accepted moves of a general-rate round: the candidates of the
+// cells in acc toggle; site (0,0) counts +2 for a minimum, -2 for a maximum.
+template <int QX, int QY, bool kTrack, int CR>
+__device__ __forceinline__ void quad_flips_acc(uint32_t (&T)[CR][4][4], const uint32_t (&cand)[CR][2][2],
+                                               const uint32_t (&acc)[CR], const uint32_t (&upc)[CR],
+                                               const TileCtx& tc, uint32_t lane, int& dh) {
+  constexpr int x0 = 2 * QX, y0 = 2 * QY;
+#pragma unroll
+  for (int row = 0; row < CR; ++row) {
+    if (kTrack && CR * lane + row == tc.cyo) {
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx)
+          if ((uint32_t)(x0 + dx) == tc.xo && (uint32_t)(y0 + dy) == tc.yo) {
+            const uint32_t f = cand[row][dy][dx] & acc[row];
+            dh += 2 * (int)(((f & upc[row]) >> tc.co) & 1u) - 2 * (int)(((f & ~upc[row]) >> tc.co) & 1u);
+          }
+    }
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx) T[row][y0 + dy][x0 + dx] ^= cand[row][dy][dx] & acc[row];
   }
 }
 
 // One single-hit round (Sec. 3.1): the quadrant set k of round r is uniform
 // over the warp, so the round dispatches once on it. The p = 1, q = 0 path
-// takes masks and flips in one branch; the general path takes the masks in
-// one branch, decides acceptance for all quadrants with the same code (one
+// takes masks and flips in one branch; the general path takes the candidates
+// in one branch, decides acceptance for all quadrants with the same code (one
 // copy of the acceptance draws), then flips in a second branch.
 // Acceptance (eq. rule, U < T with U uniform 16-bit): the top four bits of
 // every candidate come bit-sliced from one Philox block per cell row and
@@ -227,25 +307,26 @@ __device__ __forceinline__ void one_round(uint32_t (&T)[CR][4][4], const uint32_
                                           const TileCtx& tc, uint32_t lane, uint32_t r, int& dh,
                                           uint4 (&D)[CR], bool& haveD) {
   const uint32_t k = (tc.setw >> (2u * r)) & 3u;
-  uint32_t fmin[CR][2][2], fmax[CR][2][2];
   if (!kGeneral) {
+    uint32_t fmin[CR][2][2];
     switch (k) {
-      case 0: quad_masks<0, 0, false, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, fmin, fmax);
-              quad_flips<0, 0, kTrack, CR>(T, fmin, fmax, tc, lane, dh); break;
-      case 1: quad_masks<1, 0, false, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, fmin, fmax);
-              quad_flips<1, 0, kTrack, CR>(T, fmin, fmax, tc, lane, dh); break;
-      case 2: quad_masks<0, 1, false, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, fmin, fmax);
-              quad_flips<0, 1, kTrack, CR>(T, fmin, fmax, tc, lane, dh); break;
-      default: quad_masks<1, 1, false, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, fmin, fmax);
-               quad_flips<1, 1, kTrack, CR>(T, fmin, fmax, tc, lane, dh); break;
+      case 0: quad_masks<0, 0, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, fmin);
+              quad_flips<0, 0, kTrack, CR>(T, fmin, tc, lane, dh); break;
+      case 1: quad_masks<1, 0, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, fmin);
+              quad_flips<1, 0, kTrack, CR>(T, fmin, tc, lane, dh); break;
+      case 2: quad_masks<0, 1, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, fmin);
+              quad_flips<0, 1, kTrack, CR>(T, fmin, tc, lane, dh); break;
+      default: quad_masks<1, 1, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, fmin);
+               quad_flips<1, 1, kTrack, CR>(T, fmin, tc, lane, dh); break;
     }
     return;
   }
+  uint32_t cand[CR][2][2], upc[CR], uqc[CR];
   switch (k) {
-    case 0: quad_masks<0, 0, true, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, fmin, fmax); break;
-    case 1: quad_masks<1, 0, true, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, fmin, fmax); break;
-    case 2: quad_masks<0, 1, true, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, fmin, fmax); break;
-    default: quad_masks<1, 1, true, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, fmin, fmax); break;
+    case 0: quad_cands<0, 0, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, cand, upc, uqc); break;
+    case 1: quad_cands<1, 0, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, cand, upc, uqc); break;
+    case 2: quad_cands<0, 1, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, cand, upc, uqc); break;
+    default: quad_cands<1, 1, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, cand, upc, uqc); break;
   }
   const bool drawp = P.Tp != 0u && P.Tp < 65536u, drawq = P.Tq != 0u && P.Tq < 65536u;
   uint32_t AP[CR], AQ[CR], up[CR], uq[CR];
@@ -254,8 +335,8 @@ __device__ __forceinline__ void one_round(uint32_t (&T)[CR][4][4], const uint32_
   for (int row = 0; row < CR; ++row) {
     AP[row] = (P.Tp >> 16) ? ~0u : 0u;
     AQ[row] = (P.Tq >> 16) ? ~0u : 0u;
-    up[row] = drawp ? (fmin[row][0][0] | fmin[row][0][1] | fmin[row][1][0] | fmin[row][1][1]) : 0u;
-    uq[row] = drawq ? (fmax[row][0][0] | fmax[row][0][1] | fmax[row][1][0] | fmax[row][1][1]) : 0u;
+    up[row] = drawp ? upc[row] : 0u;
+    uq[row] = drawq ? uqc[row] : 0u;
     any |= up[row] | uq[row];
   }
   if (__any_sync(kFull, any != 0u)) {
@@ -293,18 +374,14 @@ __device__ __forceinline__ void one_round(uint32_t (&T)[CR][4][4], const uint32_
       }
     }
   }
+  uint32_t acc[CR];   // cells whose candidate moves
 #pragma unroll
-  for (int row = 0; row < CR; ++row) {
-#pragma unroll
-    for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-      for (int dx = 0; dx < 2; ++dx) { fmin[row][dy][dx] &= AP[row]; fmax[row][dy][dx] &= AQ[row]; }
-  }
+  for (int row = 0; row < CR; ++row) acc[row] = (upc[row] & AP[row]) | (uqc[row] & AQ[row]);
   switch (k) {
-    case 0: quad_flips<0, 0, kTrack, CR>(T, fmin, fmax, tc, lane, dh); break;
-    case 1: quad_flips<1, 0, kTrack, CR>(T, fmin, fmax, tc, lane, dh); break;
-    case 2: quad_flips<0, 1, kTrack, CR>(T, fmin, fmax, tc, lane, dh); break;
-    default: quad_flips<1, 1, kTrack, CR>(T, fmin, fmax, tc, lane, dh); break;
+    case 0: quad_flips_acc<0, 0, kTrack, CR>(T, cand, acc, upc, tc, lane, dh); break;
+    case 1: quad_flips_acc<1, 0, kTrack, CR>(T, cand, acc, upc, tc, lane, dh); break;
+    case 2: quad_flips_acc<0, 1, kTrack, CR>(T, cand, acc, upc, tc, lane, dh); break;
+    default: quad_flips_acc<1, 1, kTrack, CR>(T, cand, acc, upc, tc, lane, dh); break;
   }
 }
 

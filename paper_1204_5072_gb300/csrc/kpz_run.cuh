@@ -62,9 +62,12 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Per-warp staging in shared memory (each lane only touches its own column):
-// M: per cell row and plane, the bits of the window's two block columns that
-// lie outside the window; Pf: next block column, double-buffered; Hf: lane
-// 31's halo row, a ring of three block columns.
+// M: per cell row and plane, for the first tile the bits of block columns 0
+// and 1 that lie outside its window, from then on the carry: the low shx bits
+// of the next word to store (the top of the window just swept); Pf: block
+// columns, double-buffered (while tile t is swept, Pf[(t+1)&1] holds block
+// column t+1 as read and Pf[t&1] receives t+2); Hf: lane 31's halo row, a
+// ring of three block columns.
 template <int CR>
 struct WarpStage {
   uint32_t M[CR][kPlanes][32];
@@ -191,7 +194,8 @@ __device__ __forceinline__ void sweep_run(const SweepParams& P, WarpStage<CR>& w
 #pragma unroll
     for (int r = 0; r < CR; ++r)
 #pragma unroll
-      for (uint32_t yq = 0; yq < 4; ++yq) hx[r][yq] = (ws.M[r][yq * 4][lane] >> shx[0]) & 1u;
+      for (uint32_t yq = 0; yq < 4; ++yq)   // bit 0 of window t+1 = bit shx[0] of block column t+1
+        hx[r][yq] = ((t == 0u ? ws.M[r][yq * 4][lane] : ws.Pf[(t + 1u) & 1u][r][yq * 4][lane]) >> shx[0]) & 1u;
 #pragma unroll
     for (uint32_t xq = 0; xq < 4; ++xq)
       hy[xq] = last_lane ? __funnelshift_r(ws.Hf[t % 3u][xq], ws.Hf[(t + 1u) % 3u][xq], shx[xq]) : 0u;
@@ -231,23 +235,28 @@ __device__ __forceinline__ void sweep_run(const SweepParams& P, WarpStage<CR>& w
 
     // Write back block column t and slide the window to tile t+1.
     cp_async_wait();
-    if (!kGeneral && t != 0u && !last) {
+    if (t != 0u && !last) {
       // Interior tile: both words of each window row are this run's alone.
+      // One wide multiply-add gives the word to store, carry | T << sh, and
+      // the next carry, T >> (32 - sh) (exact: the carry is below 2^sh); the
+      // next window comes from the raw block columns t+1 and t+2 in staging.
 #pragma unroll
       for (uint32_t xq = 0; xq < 4; ++xq) {
         const uint32_t sh = shx[xq];
-        const uint32_t low = (1u << sh) - 1u;
+        const uint32_t mul = 1u << sh;
         uint32_t* cl = col(xq, t);
 #pragma unroll
         for (int r = 0; r < CR; ++r)
 #pragma unroll
           for (uint32_t yq = 0; yq < 4; ++yq) {
-            const uint32_t Tv = T[r][yq][xq], Mv = ws.M[r][yq * 4 + xq][lane];
-            __stcg(cl + offY[r][yq], (Mv & low) | (Tv << sh));                // word t
-            const uint32_t cn = (Mv & ~low) | __funnelshift_l(Tv, 0u, sh);    // word t+1
-            const uint32_t N = ws.Pf[t & 1u][r][yq * 4 + xq][lane];           // block column t+2
-            T[r][yq][xq] = __funnelshift_r(cn, N, sh);
-            ws.M[r][yq * 4 + xq][lane] = (cn & low) | (N & ~low);
+            const uint32_t pi = yq * 4 + xq;
+            unsigned long long w;
+            asm("mad.wide.u32 %0, %1, %2, %3;"
+                : "=l"(w)
+                : "r"(T[r][yq][xq]), "r"(mul), "l"((unsigned long long)ws.M[r][pi][lane]));
+            __stcg(cl + offY[r][yq], (uint32_t)w);                                    // word t
+            ws.M[r][pi][lane] = (uint32_t)(w >> 32);
+            T[r][yq][xq] = __funnelshift_r(ws.Pf[(t + 1u) & 1u][r][pi][lane], ws.Pf[t & 1u][r][pi][lane], sh);
           }
       }
     } else {
@@ -280,7 +289,7 @@ __device__ __forceinline__ void sweep_run(const SweepParams& P, WarpStage<CR>& w
             } else {
               const uint32_t N = ws.Pf[t & 1u][r][yq * 4 + xq][lane];  // block column t+2
               T[r][yq][xq] = __funnelshift_r(cn, N, sh);
-              ws.M[r][yq * 4 + xq][lane] = (cn & low) | (N & ~low);
+              ws.M[r][yq * 4 + xq][lane] = cn & low;   // the carry into word t+1
             }
           }
       }
