@@ -328,55 +328,110 @@ __device__ __forceinline__ void one_round(uint32_t (&T)[CR][4][4], const uint32_
     case 2: quad_cands<0, 1, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, cand, upc, uqc); break;
     default: quad_cands<1, 1, kPar, CR, kLive>(T, Xi, Yi, hx, hy, tc, cand, upc, uqc); break;
   }
-  const bool drawp = P.Tp != 0u && P.Tp < 65536u, drawq = P.Tq != 0u && P.Tq < 65536u;
-  uint32_t AP[CR], AQ[CR], up[CR], uq[CR];
-  uint32_t any = 0u;
-#pragma unroll
-  for (int row = 0; row < CR; ++row) {
-    AP[row] = (P.Tp >> 16) ? ~0u : 0u;
-    AQ[row] = (P.Tq >> 16) ? ~0u : 0u;
-    up[row] = drawp ? upc[row] : 0u;
-    uq[row] = drawq ? uqc[row] : 0u;
-    any |= up[row] | uq[row];
-  }
-  if (__any_sync(kFull, any != 0u)) {
-    uint32_t ties = 0u;
+  uint32_t acc[CR];   // cells whose candidate moves
+  if (kPar == 2) {
+    // Run-time parity (the batched ensemble): one compare for minima and
+    // maxima. b[n] is the threshold bit of each cell at level n (Tp's for a
+    // minimum, Tq's for a maximum); U < T from the least significant of the
+    // four levels up, lt = MAJ(~u, lt, b) per level, gives the cells decided
+    // there, and the cells equal to their threshold on all four are the ties.
+    const uint32_t dpm = (P.Tp != 0u && P.Tp < 65536u) ? ~0u : 0u;
+    const uint32_t dqm = (P.Tq != 0u && P.Tq < 65536u) ? ~0u : 0u;
+    const uint32_t pall = (P.Tp >> 16) ? ~0u : 0u, qall = (P.Tq >> 16) ? ~0u : 0u;
+    uint32_t dm[CR], any = 0u;
 #pragma unroll
     for (int row = 0; row < CR; ++row) {
-      const uint4 A = draw<kSK>(P, tc, (kTagAcc << 28) | ((CR * lane + row) << 4) | r);
-      const uint32_t w[4] = {A.x, A.y, A.z, A.w};
-      uint32_t ltp = 0u, ltq = 0u;
-#pragma unroll
-      for (uint32_t n = 0; n < 4u; ++n) {   // levels 0..3: bits 15..12 of U and T
-        const uint32_t bp = 0u - ((P.Tp >> (15u - n)) & 1u);
-        const uint32_t bq = 0u - ((P.Tq >> (15u - n)) & 1u);
-        ltp |= up[row] & ~w[n] & bp;
-        up[row] &= ~(w[n] ^ bp);
-        ltq |= uq[row] & ~w[n] & bq;
-        uq[row] &= ~(w[n] ^ bq);
-      }
-      AP[row] |= ltp;
-      AQ[row] |= ltq;
-      ties |= up[row] | uq[row];
+      dm[row] = (upc[row] & dpm) | (uqc[row] & dqm);   // candidates that need random bits
+      acc[row] = (upc[row] & pall) | (uqc[row] & qall);
+      any |= dm[row];
     }
-    if (__any_sync(kFull, ties != 0u)) {
-      if (!haveD) {
-#pragma unroll
-        for (int row = 0; row < CR; ++row)
-          D[row] = draw<kSK>(P, tc, (kTagDeep << 28) | ((CR * lane + row) << 8) | ((r & 14u) << 3));
-        haveD = true;
-      }
+    if (__any_sync(kFull, any != 0u)) {
+      uint32_t ties = 0u, tie[CR];
 #pragma unroll
       for (int row = 0; row < CR; ++row) {
-        const uint32_t acc = deep_accept<kSK>(P, tc, CR * lane + row, r, up[row], uq[row], D[row]);
-        AP[row] |= up[row] & acc;
-        AQ[row] |= uq[row] & acc;
+        const uint4 A = draw<kSK>(P, tc, (kTagAcc << 28) | ((CR * lane + row) << 4) | r);
+        const uint32_t w[4] = {A.x, A.y, A.z, A.w};
+        uint32_t b[4];
+#pragma unroll
+        for (uint32_t n = 0; n < 4u; ++n) {
+          const uint32_t bp = 0u - ((P.Tp >> (15u - n)) & 1u);
+          const uint32_t bq = 0u - ((P.Tq >> (15u - n)) & 1u);
+          b[n] = (upc[row] & bp) | (~upc[row] & bq);
+        }
+        uint32_t lt = 0u;
+#pragma unroll
+        for (int n = 3; n >= 0; --n) lt = (~w[n] & lt) | (~w[n] & b[n]) | (lt & b[n]);
+        uint32_t tq = dm[row];
+#pragma unroll
+        for (uint32_t n = 0; n < 4u; ++n) tq &= ~(w[n] ^ b[n]);
+        acc[row] |= lt & dm[row];
+        tie[row] = tq;
+        ties |= tq;
+      }
+      if (__any_sync(kFull, ties != 0u)) {
+        if (!haveD) {
+#pragma unroll
+          for (int row = 0; row < CR; ++row)
+            D[row] = draw<kSK>(P, tc, (kTagDeep << 28) | ((CR * lane + row) << 8) | ((r & 14u) << 3));
+          haveD = true;
+        }
+#pragma unroll
+        for (int row = 0; row < CR; ++row)
+          acc[row] |= deep_accept<kSK>(P, tc, CR * lane + row, r, tie[row] & upc[row], tie[row] & ~upc[row], D[row]);
       }
     }
-  }
-  uint32_t acc[CR];   // cells whose candidate moves
+  } else {
+    // Fixed parity (single lattices): minima and maxima compared separately,
+    // most significant level first (the faster form here).
+    const bool drawp = P.Tp != 0u && P.Tp < 65536u, drawq = P.Tq != 0u && P.Tq < 65536u;
+    uint32_t AP[CR], AQ[CR], up[CR], uq[CR];
+    uint32_t any = 0u;
 #pragma unroll
-  for (int row = 0; row < CR; ++row) acc[row] = (upc[row] & AP[row]) | (uqc[row] & AQ[row]);
+    for (int row = 0; row < CR; ++row) {
+      AP[row] = (P.Tp >> 16) ? ~0u : 0u;
+      AQ[row] = (P.Tq >> 16) ? ~0u : 0u;
+      up[row] = drawp ? upc[row] : 0u;
+      uq[row] = drawq ? uqc[row] : 0u;
+      any |= up[row] | uq[row];
+    }
+    if (__any_sync(kFull, any != 0u)) {
+      uint32_t ties = 0u;
+#pragma unroll
+      for (int row = 0; row < CR; ++row) {
+        const uint4 A = draw<kSK>(P, tc, (kTagAcc << 28) | ((CR * lane + row) << 4) | r);
+        const uint32_t w[4] = {A.x, A.y, A.z, A.w};
+        uint32_t ltp = 0u, ltq = 0u;
+#pragma unroll
+        for (uint32_t n = 0; n < 4u; ++n) {   // levels 0..3: bits 15..12 of U and T
+          const uint32_t bp = 0u - ((P.Tp >> (15u - n)) & 1u);
+          const uint32_t bq = 0u - ((P.Tq >> (15u - n)) & 1u);
+          ltp |= up[row] & ~w[n] & bp;
+          up[row] &= ~(w[n] ^ bp);
+          ltq |= uq[row] & ~w[n] & bq;
+          uq[row] &= ~(w[n] ^ bq);
+        }
+        AP[row] |= ltp;
+        AQ[row] |= ltq;
+        ties |= up[row] | uq[row];
+      }
+      if (__any_sync(kFull, ties != 0u)) {
+        if (!haveD) {
+#pragma unroll
+          for (int row = 0; row < CR; ++row)
+            D[row] = draw<kSK>(P, tc, (kTagDeep << 28) | ((CR * lane + row) << 8) | ((r & 14u) << 3));
+          haveD = true;
+        }
+#pragma unroll
+        for (int row = 0; row < CR; ++row) {
+          const uint32_t deep = deep_accept<kSK>(P, tc, CR * lane + row, r, up[row], uq[row], D[row]);
+          AP[row] |= up[row] & deep;
+          AQ[row] |= uq[row] & deep;
+        }
+      }
+    }
+#pragma unroll
+    for (int row = 0; row < CR; ++row) acc[row] = (upc[row] & AP[row]) | (uqc[row] & AQ[row]);
+  }
   switch (k) {
     case 0: quad_flips_acc<0, 0, kTrack, CR>(T, cand, acc, upc, tc, lane, dh); break;
     case 1: quad_flips_acc<1, 0, kTrack, CR>(T, cand, acc, upc, tc, lane, dh); break;
