@@ -82,20 +82,28 @@ def peaks():
         return 6800.0, 2070.0, "fallback"
 
 
-# ALU-pipe operations the algorithm needs per attempt at p = 1, q = 0 (bit-sliced
-# rule on 32 cells per word, 2 Philox bits per attempt, window staging):
-# 20/64 (Philox xors) + 22/32 (masks, tests, flips, neighbour shifts) + 64/512.
-K_ALG_ALU = 20 / 64 + 22 / 32 + 64 / 512
+# ALU-pipe operations the algorithm needs per attempt at p = 1, q = 0, counted
+# with three-input logic ops on 32 cells per word. Per round and cell-row word:
+# 4 per quadrant site (the two neighbour-pair tests, their AND with the
+# x-selection, the flip gated by the y-selection), 2 neighbour shifts and one
+# dead-border mask: 19/32. Philox: 20 three-input xors per 128-bit block, 2 bits
+# per attempt: 20/64. Window staging: one funnel shift per 32-site word and
+# tile to align a loaded window (the store side is one wide multiply-add on
+# the FMA pipe), 16 planes per 512 attempts: 1/32.
+K_ALG_ALU = 19 / 32 + 20 / 64 + 1 / 32
 ALU_LANES_PER_SM = 64   # integer logic pipe: 16 lanes per SM sub-partition per clock
-# General rates (p, q strictly between 0 and 1) add, per attempt: the maximum
-# test (one more logic op per quadrant site: 4/32) and the acceptance of the
-# candidates (attempted site a local minimum or maximum, density C_CAND in the
-# growth regime at p = 0.95: 0.176 minima + 0.202 maxima on oracle surfaces at
-# L = 512, t = 100..2000), which a bit-serial comparison with the threshold
+# General rates (p, q strictly between 0 and 1): per round and word, the
+# candidate test (all four neighbour bits equal: 2 per site), the selection and
+# the minimum test (1 each per site), the per-row ORs of minima and candidates
+# and the maxima (5), 2 neighbour shifts, the dead-border mask, the acceptance
+# mask (2) and the flips (4): 30/32 instead of 19/32; plus the acceptance of
+# the candidates (attempted site a local minimum or maximum, density C_CAND in
+# the growth regime at p = 0.95: 0.176 minima + 0.202 maxima on oracle surfaces
+# at L = 512, t = 100..2000), which a bit-serial comparison with the threshold
 # decides with 2 random bits on average, each costing 20/128 Philox xors and
 # 2/32 bit-sliced compare ops.
 C_CAND = 0.378
-K_ALG_ALU_GENERAL = K_ALG_ALU + 4 / 32 + C_CAND * 2 * (20 / 128 + 2 / 32)
+K_ALG_ALU_GENERAL = 30 / 32 + 20 / 64 + 1 / 32 + C_CAND * 2 * (20 / 128 + 2 / 32)
 
 
 # Files the sweep kernel is compiled from (their hash ties a profile to the source).

@@ -167,6 +167,7 @@ template <int CR>
 struct alignas(16) WarpSlot {
   run::WarpStage<CR> stage;
   SweepParams P;
+  uint4 rk[kPhiloxRounds / 2];   // Philox round keys of the item's realisation
 };
 static_assert(sizeof(WarpSlot<1>) % 16 == 0 && sizeof(WarpSlot<2>) % 16 == 0,
               "warp slots must keep 16-byte alignment");
@@ -227,6 +228,13 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(const __grid_constant__ P
     }
     const uint32_t general = re->general;
     __syncwarp();
+    // Its Philox round keys, read by the tile code from shared memory.
+    if (lane < kPhiloxRounds / 2) {
+      const uint32_t r2 = 2u * lane;
+      ws.rk[lane] = make_uint4(ws.P.k0 + r2 * kPhiloxWeylA, ws.P.k1 + r2 * kPhiloxWeylB,
+                               ws.P.k0 + (r2 + 1u) * kPhiloxWeylA, ws.P.k1 + (r2 + 1u) * kPhiloxWeylB);
+    }
+    __syncwarp();
 
     if (is_sample) {
       long long d, s1;
@@ -249,8 +257,8 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(const __grid_constant__ P
       // Device layer: this sweep's random tile origin (Sec. 3).
       const uint4 o = philox(kTagOrigin << 28, 0u, g, ws.P.sample, ws.P.k0, ws.P.k1);
       const uint32_t L = ws.P.g.L, ox = o.x & (L - 1u), oy = o.y & (L - 1u);
-      if (general) run::sweep_run<true, CR, false, true>(ws.P, ws.stage, nullptr, lane, g, ox, oy, ty, tx0, ws.P.run);
-      else         run::sweep_run<false, CR, false, true>(ws.P, ws.stage, nullptr, lane, g, ox, oy, ty, tx0, ws.P.run);
+      if (general) run::sweep_run<true, CR, true, true>(ws.P, ws.stage, ws.rk, lane, g, ox, oy, ty, tx0, ws.P.run);
+      else         run::sweep_run<false, CR, true, true>(ws.P, ws.stage, ws.rk, lane, g, ox, oy, ty, tx0, ws.P.run);
     }
     __threadfence();
     __syncwarp();
