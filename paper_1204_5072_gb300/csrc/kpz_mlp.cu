@@ -1,6 +1,7 @@
 // kpz_mlp.cu -- the learned surrogate: a 4-128-128-128-1 GELU MLP with
 // bfloat16 weights and float32 arithmetic, trained with Adam by the kernels
-// below (forward, backward, gradient reduction, update).
+// below (forward on the tcgen05 tensor cores, backward, gradient reduction,
+// update).
 //
 // The paper has no learned component. The network maps the features of a
 // realisation and a time (log2 L, log t, p, q, scaled) to log W^2; the
@@ -32,85 +33,212 @@ __device__ __forceinline__ float gelu_grad(float z) {
 }
 __device__ __forceinline__ float bf(const __nv_bfloat16* p, int i) { return __bfloat162float(p[i]); }
 
-// One dense layer for a tile of kRowsPerBlock samples: thread j computes unit j,
-// z[s] = b[j] + sum_k W[j][k] h[s][k] (h in shared memory, row stride kW).
-__device__ __forceinline__ void dense(const __nv_bfloat16* W, const __nv_bfloat16* b, const float (*h)[kW],
-                                      int j, float (&z)[kRowsPerBlock]) {
-  const float bj = bf(b, j);
+// ---------------------------------------------------------------------------
+// Forward pass on the 5th-generation tensor cores (tcgen05). A tile is 128
+// samples, one thread per sample. The two 128 x 128 layers run as
+// D[s][j] = sum_k A[s][k] W[j][k] with M = N = K = 128: A (activations) and W
+// (weights) in shared memory in the canonical K-major layout without swizzle
+// (8-row x 16-byte core matrices, 128 B apart along K, 2048 B apart along the
+// rows), the float32 accumulator in tensor memory (lane = sample, column =
+// unit). The MMA takes bfloat16 operands; the weights are bfloat16 already,
+// each float32 activation a is split into hi = bf16(a) and lo = bf16(a - hi),
+// and two chains of MMAs (hi, then lo, 8 of K = 16 each) accumulate
+// sum_k (hi + lo) W, which agrees with the float32 product to about 2^-16
+// relative. One thread issues the MMAs and commits them to an mbarrier; every
+// wait on it is bounded in time (a timeout sets *err and the host reports it).
+namespace tc {
+
+constexpr int kM = 128;                              // samples per tile (MMA M)
+constexpr uint32_t kOpBytes = (uint32_t)kW * kW * 2;  // one 128 x 128 bfloat16 operand
+constexpr size_t kSmem = 3 * (size_t)kOpBytes;       // A hi, A lo, W
+// Instruction descriptor of tcgen05.mma kind::f16: float32 accumulator
+// (bits 4-5 = 1), bfloat16 A and B (bits 7-9, 10-12 = 1), both K-major,
+// N / 8 at bits 17-22, M / 16 at bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kW >> 3) << 17) |
+                            ((uint32_t)(kM >> 4) << 24);
+constexpr uint64_t kWaitNs = 1000000000ull;          // bound of every wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Byte offset of element (row, k) of a 128 x 128 bfloat16 operand.
+__device__ __forceinline__ uint32_t cm_off(int row, int k) {
+  return (uint32_t)(((row >> 3) * 16 + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// Shared-memory matrix descriptor: start address, leading-dimension byte
+// offset (between core matrices along K: 128), stride byte offset (between
+// 8-row groups: 2048), descriptor version 1 (bit 46), no swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(2048u >> 4) << 32) |
+         (1ull << 46);
+}
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// D (tensor memory) = (Ahi + Alo) W^T over K = 128, then commit to mbar.
+__device__ __forceinline__ void mma_chain(uint32_t taddr, uint32_t ahi, uint32_t alo, uint32_t b, uint32_t mbar) {
 #pragma unroll
-  for (int s = 0; s < kRowsPerBlock; ++s) z[s] = bj;
-  const __nv_bfloat16* row = W + j * kW;
-#pragma unroll 1
-  for (int k0 = 0; k0 < kW; k0 += 8) {
-    float w[8];
+  for (int part = 0; part < 2; ++part) {
 #pragma unroll
-    for (int kk = 0; kk < 8; ++kk) w[kk] = bf(row, k0 + kk);
-#pragma unroll
-    for (int s = 0; s < kRowsPerBlock; ++s) {
-      const float4 a = *reinterpret_cast<const float4*>(&h[s][k0]);
-      const float4 c = *reinterpret_cast<const float4*>(&h[s][k0 + 4]);
-      z[s] += w[0] * a.x + w[1] * a.y + w[2] * a.z + w[3] * a.w + w[4] * c.x + w[5] * c.y + w[6] * c.z +
-              w[7] * c.w;
+    for (int kk = 0; kk < kW / 16; ++kk) {
+      const uint64_t ad = sdesc((part ? alo : ahi) + kk * 256u);
+      const uint64_t bd = sdesc(b + kk * 256u);
+      const uint32_t acc = (part | kk) ? 1u : 0u;
+      asm volatile(
+          "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
+          "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
     }
+  }
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+// Wait until phase `parity` of the mbarrier has completed; false on timeout.
+__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity) {
+  const uint64_t t0 = gtimer();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (gtimer() - t0 > kWaitNs) return false;
   }
 }
 
-// Forward pass of a tile: y (and, for training, the pre-activations z1..z3).
-__global__ void __launch_bounds__(kW) fwd_kernel(const __nv_bfloat16* __restrict__ P, const float* __restrict__ x,
-                                                 int n, float* __restrict__ y, float* __restrict__ zsave) {
-  __shared__ __align__(16) float hA[kRowsPerBlock][kW];
-  __shared__ __align__(16) float hB[kRowsPerBlock][kW];
-  __shared__ float xs[kRowsPerBlock][kIn];
-  __shared__ float part[kW / 32][kRowsPerBlock];
-  const int j = threadIdx.x, s0 = blockIdx.x * kRowsPerBlock;
-  for (int e = j; e < kRowsPerBlock * kIn; e += kW) {
-    const int s = e / kIn, c = e % kIn;
-    xs[s][c] = (s0 + s < n) ? x[(size_t)(s0 + s) * kIn + c] : 0.f;
+// 32 consecutive float32 columns of this warp's 32 tensor-memory lanes.
+__device__ __forceinline__ void ld32(uint32_t ta, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(ta));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Eight activations h[0..7] of units j0..j0+7 (j0 % 8 == 0) of sample row s,
+// split into bfloat16 hi and lo parts, as one 16-byte core-matrix row each.
+__device__ __forceinline__ void put8(unsigned char* Ahi, unsigned char* Alo, int s, int j0, const float* h) {
+  __align__(16) __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    hi[i] = __float2bfloat16_rn(h[i]);
+    lo[i] = __float2bfloat16_rn(h[i] - __bfloat162float(hi[i]));
   }
+  *reinterpret_cast<uint4*>(Ahi + cm_off(s, j0)) = *reinterpret_cast<const uint4*>(hi);
+  *reinterpret_cast<uint4*>(Alo + cm_off(s, j0)) = *reinterpret_cast<const uint4*>(lo);
+}
+
+// W (128 x 128 bfloat16, row = output unit, K contiguous) into the operand layout.
+__device__ __forceinline__ void stage_w(unsigned char* Bs, const __nv_bfloat16* W, int t) {
+#pragma unroll 4
+  for (int q = t; q < kW * kW / 8; q += kM) {
+    const int row = q >> 4, k0 = (q & 15) * 8;
+    *reinterpret_cast<uint4*>(Bs + cm_off(row, k0)) = *reinterpret_cast<const uint4*>(W + row * kW + k0);
+  }
+}
+
+__device__ __forceinline__ void fence_to_mma() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  float z[kRowsPerBlock];
-  {
-    float w[kIn];
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+}  // namespace tc
+
+// Forward pass of a tile of 128 samples: y (and, for training, the
+// pre-activations z1..z3 in zsave).
+__global__ void __launch_bounds__(tc::kM, 1) fwd_kernel(const __nv_bfloat16* __restrict__ P,
+                                                        const float* __restrict__ x, int n, float* __restrict__ y,
+                                                        float* __restrict__ zsave, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_tc[];
+  unsigned char* Ahi = smem_tc;
+  unsigned char* Alo = smem_tc + tc::kOpBytes;
+  unsigned char* Bs = smem_tc + 2 * tc::kOpBytes;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t taddr_s;
+  const int s = threadIdx.x, warp = s >> 5;
+  const int gs = blockIdx.x * tc::kM + s;
+  const bool live = gs < n;
+  float xin[kIn];
 #pragma unroll
-    for (int c = 0; c < kIn; ++c) w[c] = bf(P + oW1, j * kIn + c);
-    const float bj = bf(P + oB1, j);
+  for (int c = 0; c < kIn; ++c) xin[c] = live ? x[(size_t)gs * kIn + c] : 0.f;
+  // Layer 1 (K = 4) on the CUDA cores, straight into the operand A.
+#pragma unroll 1
+  for (int j0 = 0; j0 < kW; j0 += 8) {
+    float h[8];
 #pragma unroll
-    for (int s = 0; s < kRowsPerBlock; ++s) {
-      float a = bj;
+    for (int i = 0; i < 8; ++i) {
+      const int j = j0 + i;
+      float z = bf(P + oB1, j);
 #pragma unroll
-      for (int c = 0; c < kIn; ++c) a += w[c] * xs[s][c];
-      z[s] = a;
+      for (int c = 0; c < kIn; ++c) z += bf(P + oW1, j * kIn + c) * xin[c];
+      if (zsave && live) zsave[((size_t)gs * 3 + 0) * kW + j] = z;
+      h[i] = gelu(z);
+    }
+    tc::put8(Ahi, Alo, s, j0, h);
+  }
+  tc::stage_w(Bs, P + oW2, s);
+  if (s == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&mbar)));
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(tc::smem_u32(&taddr_s)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc::fence_to_mma();
+  const uint32_t taddr = taddr_s, lanes = taddr + ((uint32_t)(warp * 32) << 16);
+  const uint32_t mb = tc::smem_u32(&mbar);
+  bool ok = true;
+  const int oBl[2] = {oB2, oB3};
+  float out = 0.f;
+#pragma unroll 1
+  for (int layer = 0; layer < 2; ++layer) {
+    if (s == 0) tc::mma_chain(taddr, tc::smem_u32(Ahi), tc::smem_u32(Alo), tc::smem_u32(Bs), mb);
+    ok = tc::wait_phase(mb, (uint32_t)layer) && ok;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+    for (int c = 0; c < kW; c += 32) {
+      float v[32];
+      tc::ld32(lanes + (uint32_t)c, v);
+#pragma unroll
+      for (int g = 0; g < 32; g += 8) {
+        float h[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int j = c + g + i;
+          const float z = v[g + i] + bf(P + oBl[layer], j);
+          if (zsave && live) zsave[((size_t)gs * 3 + 1 + layer) * kW + j] = z;
+          h[i] = gelu(z);
+          if (layer == 1) out += bf(P + oW4, j) * h[i];
+        }
+        if (layer == 0) tc::put8(Ahi, Alo, s, c + g, h);
+      }
+    }
+    if (layer == 0) {
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();   // every lane read layer 2 and the MMAs are done with W2: restage
+      tc::stage_w(Bs, P + oW3, s);
+      tc::fence_to_mma();
     }
   }
-  auto store = [&](int layer, float (*h)[kW]) {
-#pragma unroll
-    for (int s = 0; s < kRowsPerBlock; ++s) {
-      if (zsave && s0 + s < n) zsave[((size_t)(s0 + s) * 3 + layer) * kW + j] = z[s];
-      h[s][j] = gelu(z[s]);
-    }
-  };
-  store(0, hA);
+  if (live) y[gs] = out + bf(P + oB4, 0);
+  if (!ok) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  dense(P + oW2, P + oB2, hA, j, z);
-  store(1, hB);
-  __syncthreads();
-  dense(P + oW3, P + oB3, hB, j, z);
-  const float w4 = bf(P + oW4, j);
-#pragma unroll
-  for (int s = 0; s < kRowsPerBlock; ++s) {
-    if (zsave && s0 + s < n) zsave[((size_t)(s0 + s) * 3 + 2) * kW + j] = z[s];
-    float v = w4 * gelu(z[s]);
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-    if ((j & 31) == 0) part[j >> 5][s] = v;
-  }
-  __syncthreads();
-  if (j < kRowsPerBlock && s0 + j < n) {
-    float v = bf(P + oB4, 0);
-#pragma unroll
-    for (int q = 0; q < kW / 32; ++q) v += part[q][j];
-    y[s0 + j] = v;
-  }
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(taddr));
 }
 
 // Backward pass of a tile: d(mean squared error)/d(parameters) restricted to
@@ -268,6 +396,7 @@ struct kpz_mlp {
   // per-call buffers: data (x, t) for `cap` samples, work (y, z, gpart) for `wcap`
   float *x = nullptr, *t = nullptr, *y = nullptr, *z = nullptr, *gpart = nullptr;
   size_t cap = 0, wcap = 0;
+  int* err = nullptr;           // set by the forward kernel when a tensor-core wait timed out
 };
 
 namespace {
@@ -276,6 +405,21 @@ void mlp_release(kpz_mlp* m) {
   float* ptrs[] = {m->theta, m->m, m->v, m->grad, m->x, m->t, m->y, m->z, m->gpart};
   for (float* p : ptrs) if (p) cudaFree(p);
   if (m->P) cudaFree(m->P);
+  if (m->err) cudaFree(m->err);
+}
+
+// KPZ_OK, or KPZ_ETIMEOUT when a forward kernel's tensor-core wait ran out
+// (the flag is then cleared); the stream is synchronised.
+kpz_status check_err(kpz_mlp* m) {
+  int e = 0;
+  if (cudaMemcpyAsync(&e, m->err, 4, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
+      cudaStreamSynchronize(m->stream) != cudaSuccess)
+    return KPZ_ECUDA;
+  if (e) {
+    cudaMemsetAsync(m->err, 0, 4, m->stream);
+    return KPZ_ETIMEOUT;
+  }
+  return KPZ_OK;
 }
 
 // Data buffers for n samples and work buffers for passes over w samples.
@@ -311,7 +455,7 @@ kpz_status ensure(kpz_mlp* m, size_t n, size_t w) {
 // data into m->grad; y and z are filled on the way.
 cudaError_t grad_pass(kpz_mlp* m, const float* x, const float* t, int n) {
   const int tiles = (n + kRowsPerBlock - 1) / kRowsPerBlock;
-  fwd_kernel<<<tiles, kW, 0, m->stream>>>(m->P, x, n, m->y, m->z);
+  fwd_kernel<<<(n + tc::kM - 1) / tc::kM, tc::kM, tc::kSmem, m->stream>>>(m->P, x, n, m->y, m->z, m->err);
   count_launch();
   bwd_kernel<<<tiles, kW, kBwdSmem, m->stream>>>(m->P, x, t, m->y, m->z, n, 1.f / (float)n, m->gpart);
   count_launch();
@@ -335,13 +479,15 @@ kpz_status kpz_mlp_create(kpz_mlp** out, const float* params, void* stream) {
   m->stream = (cudaStream_t)stream;
   if (cudaMalloc(&m->theta, kParams * 4) != cudaSuccess || cudaMalloc(&m->m, kParams * 4) != cudaSuccess ||
       cudaMalloc(&m->v, kParams * 4) != cudaSuccess || cudaMalloc(&m->grad, kPart * 4) != cudaSuccess ||
-      cudaMalloc(&m->P, kParams * 2) != cudaSuccess) {
+      cudaMalloc(&m->P, kParams * 2) != cudaSuccess || cudaMalloc(&m->err, 4) != cudaSuccess) {
     cudaGetLastError();
     mlp_release(m);
     delete m;
     return KPZ_ENOMEM;
   }
   if (cudaFuncSetAttribute(bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmem) != cudaSuccess ||
+      cudaMemsetAsync(m->err, 0, 4, m->stream) != cudaSuccess ||
       cudaMemcpyAsync(m->theta, params, kParams * 4, cudaMemcpyHostToDevice, m->stream) != cudaSuccess ||
       cudaMemsetAsync(m->m, 0, kParams * 4, m->stream) != cudaSuccess ||
       cudaMemsetAsync(m->v, 0, kParams * 4, m->stream) != cudaSuccess) {
@@ -373,16 +519,15 @@ kpz_status kpz_mlp_predict(kpz_mlp* m, const float* x, uint32_t n, float* y) {
   if (n == 0) return KPZ_OK;
   kpz_status st = ensure(m, n, n);
   if (st) return st;
-  const int tiles = (int)((n + kRowsPerBlock - 1) / kRowsPerBlock);
   if (cudaMemcpyAsync(m->x, x, (size_t)n * kIn * 4, cudaMemcpyHostToDevice, m->stream) != cudaSuccess)
     return KPZ_ECUDA;
-  fwd_kernel<<<tiles, kW, 0, m->stream>>>(m->P, m->x, (int)n, m->y, nullptr);
+  fwd_kernel<<<(n + tc::kM - 1) / tc::kM, tc::kM, tc::kSmem, m->stream>>>(m->P, m->x, (int)n, m->y, nullptr,
+                                                                         m->err);
   count_launch();
   if (cudaGetLastError() != cudaSuccess ||
-      cudaMemcpyAsync(y, m->y, (size_t)n * 4, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
-      cudaStreamSynchronize(m->stream) != cudaSuccess)
+      cudaMemcpyAsync(y, m->y, (size_t)n * 4, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess)
     return KPZ_ECUDA;
-  return KPZ_OK;
+  return check_err(m);
 }
 
 kpz_status kpz_mlp_loss_grad(kpz_mlp* m, const float* x, const float* t, uint32_t n, float* loss, float* grad) {
@@ -399,7 +544,7 @@ kpz_status kpz_mlp_loss_grad(kpz_mlp* m, const float* x, const float* t, uint32_
     return KPZ_ECUDA;
   if (grad) for (int i = 0; i < kParams; ++i) grad[i] = h[i];
   if (loss) *loss = h[kParams] / (float)n;
-  return KPZ_OK;
+  return check_err(m);
 }
 
 kpz_status kpz_mlp_train(kpz_mlp* m, const float* x, const float* t, uint32_t n, const uint32_t* order,
@@ -435,7 +580,7 @@ kpz_status kpz_mlp_train(kpz_mlp* m, const float* x, const float* t, uint32_t n,
       cudaStreamSynchronize(m->stream) != cudaSuccess)
     return KPZ_ECUDA;
   if (last_loss) *last_loss = sq / (float)batch;
-  return KPZ_OK;
+  return check_err(m);
 }
 
 void kpz_mlp_free(kpz_mlp* m) {
