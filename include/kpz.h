@@ -285,7 +285,10 @@ void kpz_batch_free(kpz_batch* b);
  * W1 (128 x 4, row-major), b1 (128), W2 (128 x 128), b2, W3 (128 x 128), b3,
  * w4 (128), b4 (1). Inputs: n rows of 4 float32 features; targets: n float32.
  * The loss is the mean squared error. Gradients are reduced in a fixed order:
- * a call with the same inputs gives the same result.                       */
+ * a call with the same inputs gives the same result. The 128 x 128 layers run
+ * on the tcgen05 tensor cores with waits bounded in time: predict, loss_grad
+ * and train return KPZ_ETIMEOUT if one ran out (the results are then
+ * invalid; the handle stays usable), KPZ_ECUDA on a CUDA error.            */
 typedef struct kpz_mlp kpz_mlp;
 /* Upload initial parameters (caller-chosen initialisation); stream may be NULL. */
 kpz_status kpz_mlp_create(kpz_mlp** out, const float* params, void* stream);
