@@ -1,7 +1,7 @@
 // kpz_mlp.cu -- the learned surrogate: a 4-128-128-128-1 GELU MLP with
 // bfloat16 weights and float32 arithmetic, trained with Adam by the kernels
-// below (forward on the tcgen05 tensor cores, backward, gradient reduction,
-// update).
+// below (forward and backward on the tcgen05 tensor cores, gradient
+// reduction, update).
 //
 // The paper has no learned component. The network maps the features of a
 // realisation and a time (log2 L, log t, p, q, scaled) to log W^2; the
@@ -21,7 +21,7 @@
 namespace kpz {
 namespace mlp {
 
-constexpr int kW = 128, kIn = 4, kRowsPerBlock = 32;
+constexpr int kW = 128, kIn = 4;
 constexpr int oW1 = 0, oB1 = oW1 + kW * kIn, oW2 = oB1 + kW, oB2 = oW2 + kW * kW, oW3 = oB2 + kW,
               oB3 = oW3 + kW * kW, oW4 = oB3 + kW, oB4 = oW4 + kW, kParams = oB4 + 1;
 static_assert(kParams == 33793, "parameter count");
@@ -241,109 +241,220 @@ __global__ void __launch_bounds__(tc::kM, 1) fwd_kernel(const __nv_bfloat16* __r
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(taddr));
 }
 
-// Backward pass of a tile: d(mean squared error)/d(parameters) restricted to
-// the tile's samples, written to its own slot of gpart (no atomics).
-__global__ void __launch_bounds__(kW) bwd_kernel(const __nv_bfloat16* __restrict__ P, const float* __restrict__ x,
-                                                 const float* __restrict__ t, const float* __restrict__ y,
-                                                 const float* __restrict__ zsave, int n, float inv_n,
-                                                 float* __restrict__ gpart) {
-  extern __shared__ __align__(16) float sm[];
-  float (*hprev)[kW] = reinterpret_cast<float (*)[kW]>(sm);              // input of the layer
-  float (*dz)[kW] = reinterpret_cast<float (*)[kW]>(sm + kRowsPerBlock * kW);     // gradient at its output
-  float (*zl)[kW] = reinterpret_cast<float (*)[kW]>(sm + 2 * kRowsPerBlock * kW); // its pre-activation
-  float* dy = sm + 3 * kRowsPerBlock * kW;                                        // kRowsPerBlock
-  float* xs = dy + kRowsPerBlock;                                                 // kRowsPerBlock * kIn
-  const int j = threadIdx.x, s0 = blockIdx.x * kRowsPerBlock;
-  float* g = gpart + (size_t)blockIdx.x * kPart;
-  for (int e = j; e < kRowsPerBlock * kIn; e += kW) {
-    const int s = e / kIn;
-    xs[e] = (s0 + s < n) ? x[(size_t)(s0 + s) * kIn + e % kIn] : 0.f;
+namespace tc {
+
+// D (tensor memory) = sum over the npair operand pairs (a[i], b[i]) of
+// a[i] b[i]^T, K = 128 each, then commit to mbar.
+__device__ __forceinline__ void mma_pairs(uint32_t taddr, const uint32_t* a, const uint32_t* b, int npair,
+                                          uint32_t mbar) {
+#pragma unroll 1
+  for (int pr = 0; pr < npair; ++pr) {
+#pragma unroll
+    for (int kk = 0; kk < kW / 16; ++kk) {
+      const uint64_t ad = sdesc(a[pr] + kk * 256u);
+      const uint64_t bd = sdesc(b[pr] + kk * 256u);
+      const uint32_t acc = (pr | kk) ? 1u : 0u;
+      asm volatile(
+          "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
+          "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+    }
   }
-  if (j < kRowsPerBlock) {
-    const float r = (s0 + j < n) ? (y[s0 + j] - t[s0 + j]) : 0.f;
-    dy[j] = 2.f * r * inv_n;
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+// Element (row, k) of a pair of operands as bfloat16 hi and lo parts.
+__device__ __forceinline__ void put1(unsigned char* Xhi, unsigned char* Xlo, int row, int k, float v) {
+  const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+  *reinterpret_cast<__nv_bfloat16*>(Xhi + cm_off(row, k)) = hi;
+  *reinterpret_cast<__nv_bfloat16*>(Xlo + cm_off(row, k)) = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+__device__ __forceinline__ float get1(const unsigned char* Xhi, const unsigned char* Xlo, int row, int k) {
+  return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(Xhi + cm_off(row, k))) +
+         __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(Xlo + cm_off(row, k)));
+}
+
+// W^T of a 128 x 128 bfloat16 weight matrix (row = output unit) into the
+// operand layout: element (k, u) = W[u][k].
+__device__ __forceinline__ void stage_wt(unsigned char* Bs, const __nv_bfloat16* W, int t) {
+#pragma unroll 2
+  for (int q = t; q < kW * kW / 8; q += kM) {
+    const int k = q & (kW - 1), u0 = (q >> 7) * 8;
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = W[(u0 + i) * kW + k];
+    *reinterpret_cast<uint4*>(Bs + cm_off(k, u0)) = *reinterpret_cast<const uint4*>(v);
+  }
+}
+
+}  // namespace tc
+
+// Backward pass of a tile of 128 samples: d(mean squared error)/d(parameters)
+// restricted to the tile's samples, written to its own slot of gpart (no
+// atomics). Per hidden layer (3, then 2) two tensor-core products: the weight
+// gradient dW[u][k] = sum_s dz[s][u] h[s][k] (M = units, K = samples; dz and h
+// split into bfloat16 hi and lo, three MMA chains hi.hi + hi.lo + lo.hi, in
+// tensor-memory columns 128..255) and the gradient at the layer's input
+// dh[s][k] = sum_u dz[s][u] W[u][k] (M = samples, K = units; two chains, in
+// columns 0..127). Column sums over the samples (biases, the output and the
+// first layer) are taken by one thread per unit in sample order.
+__global__ void __launch_bounds__(tc::kM, 1) bwd_kernel(const __nv_bfloat16* __restrict__ P,
+                                                        const float* __restrict__ x, const float* __restrict__ t,
+                                                        const float* __restrict__ y, const float* __restrict__ zsave,
+                                                        int n, float inv_n, float* __restrict__ gpart,
+                                                        int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_tc[];
+  unsigned char* X0 = smem_tc;                       // operand buffers, 32 KB each
+  unsigned char* X1 = smem_tc + tc::kOpBytes;
+  unsigned char* X2 = smem_tc + 2 * tc::kOpBytes;
+  unsigned char* X3 = smem_tc + 3 * tc::kOpBytes;
+  float* dzT = reinterpret_cast<float*>(smem_tc);    // layer 1: dz1 as [unit][sample] float32 (X0, X1)
+  __shared__ float dy[tc::kM];
+  __shared__ float xs[tc::kM * kIn];
+  __shared__ float sq_part[tc::kM / 32];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t taddr_s;
+  const int s = threadIdx.x, warp = s >> 5;   // thread = sample s of the tile, or unit u = s
+  const int s0 = blockIdx.x * tc::kM, gs = s0 + s;
+  const bool live = gs < n;
+  float* g = gpart + (size_t)blockIdx.x * kPart;
+  auto zval = [&](int smp, int layer, int u) -> float {   // zero beyond the last sample
+    return (s0 + smp < n) ? zsave[((size_t)(s0 + smp) * 3 + layer) * kW + u] : 0.f;
+  };
+#pragma unroll
+  for (int c = 0; c < kIn; ++c) xs[s * kIn + c] = live ? x[(size_t)gs * kIn + c] : 0.f;
+  {
+    const float r = live ? (y[gs] - t[gs]) : 0.f;
+    dy[s] = 2.f * r * inv_n;
     float sq = r * r;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, d);
-    if (j == 0) g[kParams] = sq;
+    if ((s & 31) == 0) sq_part[warp] = sq;
   }
-  auto zval = [&](int s, int layer, int u) -> float {
-    return (s0 + s < n) ? zsave[((size_t)(s0 + s) * 3 + layer) * kW + u] : 0.f;
-  };
-  // Output layer: dz3 = dy * w4 * gelu'(z3); grads of w4, b4.
-  for (int s = 0; s < kRowsPerBlock; ++s) {
-    zl[s][j] = zval(s, 2, j);
-    hprev[s][j] = gelu(zval(s, 1, j));
+  if (s == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&mbar)));
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(tc::smem_u32(&taddr_s)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t taddr = taddr_s, lanes = taddr + ((uint32_t)(warp * 32) << 16);
+  const uint32_t mb = tc::smem_u32(&mbar);
+  const uint32_t x0 = tc::smem_u32(X0), x1 = tc::smem_u32(X1), x2 = tc::smem_u32(X2), x3 = tc::smem_u32(X3);
+  uint32_t phase = 0;
+  bool ok = true;
+  if (s == 0) g[kParams] = sq_part[0] + sq_part[1] + sq_part[2] + sq_part[3];
+  // Output layer (unit u = s): grads of w4 and b4, in sample order.
   {
-    const float w4 = bf(P + oW4, j);
-    float gw4 = 0.f;
-    for (int s = 0; s < kRowsPerBlock; ++s) {
-      gw4 += dy[s] * gelu(zl[s][j]);
-      dz[s][j] = dy[s] * w4 * gelu_grad(zl[s][j]);
+    float gw4 = 0.f, gb = 0.f;
+    for (int k = 0; k < tc::kM; ++k) {
+      gw4 += dy[k] * gelu(zval(k, 2, s));
+      gb += dy[k];
     }
-    g[oW4 + j] = gw4;
-    if (j == 0) {
-      float gb = 0.f;
-      for (int s = 0; s < kRowsPerBlock; ++s) gb += dy[s];
-      g[oB4] = gb;
-    }
+    g[oW4 + s] = gw4;
+    if (s == 0) g[oB4] = gb;
   }
-  __syncthreads();
-  // Hidden layers 3 and 2: grads of W, b; then the gradient at the input.
   const int oW[2] = {oW3, oW2}, oB[2] = {oB3, oB2};
 #pragma unroll 1
   for (int L = 0; L < 2; ++L) {
-    // dW[j][k] = sum_s dz[s][j] hprev[s][k]; db[j] = sum_s dz[s][j]
-    float db = 0.f;
-    for (int s = 0; s < kRowsPerBlock; ++s) db += dz[s][j];
-    g[oB[L] + j] = db;
+    const int zl = 2 - L;   // pre-activation of this layer's output: z3, then z2
+    // dz (sample s) -> X0/X1 transposed (row = unit), h at the layer's input -> X2/X3 transposed.
+    // Layer 3: dz3 = dy w4 gelu'(z3); layer 2: dz2 = dh2 gelu'(z2), dh2 from tensor memory.
 #pragma unroll 1
-    for (int k0 = 0; k0 < kW; k0 += 8) {
-      float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      for (int s = 0; s < kRowsPerBlock; ++s) {
-        const float d = dz[s][j];
+    for (int c = 0; c < kW; c += 32) {
+      float dh[32];
+      if (L == 1) tc::ld32(lanes + (uint32_t)c, dh);
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) a[kk] += d * hprev[s][k0 + kk];
+      for (int i = 0; i < 32; ++i) {
+        const int u = c + i;
+        const float d = (L == 0) ? dy[s] * bf(P + oW4, u) : dh[i];
+        tc::put1(X0, X1, u, s, d * gelu_grad(zval(s, zl, u)));
+        tc::put1(X2, X3, u, s, gelu(zval(s, zl - 1, u)));
       }
-#pragma unroll
-      for (int kk = 0; kk < 8; ++kk) g[oW[L] + j * kW + k0 + kk] = a[kk];
     }
-    // gradient at the input of this layer: dh[s][k] = sum_u W[u][k] dz[s][u]  (thread k)
-    float dh[kRowsPerBlock];
-#pragma unroll
-    for (int s = 0; s < kRowsPerBlock; ++s) dh[s] = 0.f;
-    const __nv_bfloat16* W = P + oW[L];
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    tc::fence_to_mma();
+    // Bias gradient (unit u = s): column sum of dz in sample order.
+    {
+      float db = 0.f;
+      for (int k = 0; k < tc::kM; ++k) db += tc::get1(X0, X1, s, k);
+      g[oB[L] + s] = db;
+    }
+    __syncthreads();   // every column read before X0/X1 are rewritten below
+    // dW[u][k] into columns 128..255.
+    if (s == 0) {
+      const uint32_t a[3] = {x0, x0, x1}, b[3] = {x2, x3, x2};
+      tc::mma_pairs(taddr + 128u, a, b, 3, mb);
+    }
+    ok = tc::wait_phase(mb, phase) && ok;
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll 1
-    for (int u = 0; u < kW; ++u) {
-      const float w = bf(W, u * kW + j);
+    for (int c = 0; c < kW; c += 32) {
+      float v[32];
+      tc::ld32(lanes + 128u + (uint32_t)c, v);
+      float* dst = g + oW[L] + s * kW + c;   // a tile's slot is not 16-byte aligned: scalar stores
 #pragma unroll
-      for (int s = 0; s < kRowsPerBlock; ++s) dh[s] += w * dz[s][u];
+      for (int i = 0; i < 32; ++i) dst[i] = v[i];
     }
-    __syncthreads();   // everyone is done with dz, hprev and zl of this layer
-    const int below = 1 - L;   // pre-activation index of the layer whose output we reach
+    // dz again, now as rows (sample s) in X0/X1; W^T in X2.
+#pragma unroll 1
+    for (int c = 0; c < kW; c += 32) {
+      float dh[32];
+      if (L == 1) tc::ld32(lanes + (uint32_t)c, dh);
 #pragma unroll
-    for (int s = 0; s < kRowsPerBlock; ++s) {
-      const float zb = zval(s, below, j);
-      dz[s][j] = dh[s] * gelu_grad(zb);
-      if (L == 0) hprev[s][j] = gelu(zval(s, 0, j));   // input of layer 2 = h1
+      for (int g8 = 0; g8 < 32; g8 += 8) {
+        float d8[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int u = c + g8 + i;
+          const float d = (L == 0) ? dy[s] * bf(P + oW4, u) : dh[g8 + i];
+          d8[i] = d * gelu_grad(zval(s, zl, u));
+        }
+        tc::put8(X0, X1, s, c + g8, d8);
+      }
     }
+    tc::stage_wt(X2, P + oW[L], s);
+    tc::fence_to_mma();
+    // dh at the layer's input into columns 0..127.
+    if (s == 0) {
+      const uint32_t a[2] = {x0, x1}, b[2] = {x2, x2};
+      tc::mma_pairs(taddr, a, b, 2, mb);
+    }
+    ok = tc::wait_phase(mb, phase) && ok;
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
   }
-  // First layer: dW1[j][c] = sum_s dz1[s][j] x[s][c]; db1[j] = sum_s dz1[s][j]
+  // First layer: dz1 = dh1 gelu'(z1) (sample s) into dzT[u][s], then per unit u
+  // dW1[u][c] = sum_s dz1 x[s][c], db1[u] = sum_s dz1, in sample order.
+#pragma unroll 1
+  for (int c = 0; c < kW; c += 32) {
+    float dh[32];
+    tc::ld32(lanes + (uint32_t)c, dh);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) dzT[(c + i) * tc::kM + s] = dh[i] * gelu_grad(zval(s, 0, c + i));
+  }
+  __syncthreads();
   {
     float a[kIn] = {0.f, 0.f, 0.f, 0.f}, db = 0.f;
-    for (int s = 0; s < kRowsPerBlock; ++s) {
-      const float d = dz[s][j];
+    for (int k = 0; k < tc::kM; ++k) {
+      const float d = dzT[s * tc::kM + k];
       db += d;
 #pragma unroll
-      for (int c = 0; c < kIn; ++c) a[c] += d * xs[s * kIn + c];
+      for (int c = 0; c < kIn; ++c) a[c] += d * xs[k * kIn + c];
     }
 #pragma unroll
-    for (int c = 0; c < kIn; ++c) g[oW1 + j * kIn + c] = a[c];
-    g[oB1 + j] = db;
+    for (int c = 0; c < kIn; ++c) g[oW1 + s * kIn + c] = a[c];
+    g[oB1 + s] = db;
   }
+  if (!ok) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(taddr));
 }
 
 // grad[i] = sum over tiles b of gpart[b][i], tiles in order (deterministic).
@@ -376,7 +487,7 @@ __global__ void to_bf16_kernel(const float* __restrict__ theta, __nv_bfloat16* _
   if (i < kParams) P[i] = __float2bfloat16_rn(theta[i]);
 }
 
-constexpr size_t kBwdSmem = (3 * kRowsPerBlock * kW + kRowsPerBlock + kRowsPerBlock * kIn) * sizeof(float);
+constexpr size_t kBwdSmem = 4 * (size_t)tc::kOpBytes;   // four tensor-core operand buffers
 
 }  // namespace mlp
 }  // namespace kpz
@@ -440,7 +551,7 @@ kpz_status ensure(kpz_mlp* m, size_t n, size_t w) {
     for (float* p : bufs) if (p) cudaFree(p);
     m->y = m->z = m->gpart = nullptr;
     m->wcap = 0;
-    const size_t tiles = (w + kRowsPerBlock - 1) / kRowsPerBlock;
+    const size_t tiles = (w + tc::kM - 1) / tc::kM;
     if (cudaMalloc(&m->y, w * 4) != cudaSuccess || cudaMalloc(&m->z, w * 3 * kW * 4) != cudaSuccess ||
         cudaMalloc(&m->gpart, tiles * kPart * 4) != cudaSuccess) {
       cudaGetLastError();
@@ -454,10 +565,11 @@ kpz_status ensure(kpz_mlp* m, size_t n, size_t w) {
 // Gradient of the mean squared error over samples [0, n) of the uploaded
 // data into m->grad; y and z are filled on the way.
 cudaError_t grad_pass(kpz_mlp* m, const float* x, const float* t, int n) {
-  const int tiles = (n + kRowsPerBlock - 1) / kRowsPerBlock;
-  fwd_kernel<<<(n + tc::kM - 1) / tc::kM, tc::kM, tc::kSmem, m->stream>>>(m->P, x, n, m->y, m->z, m->err);
+  const int tiles = (n + tc::kM - 1) / tc::kM;
+  fwd_kernel<<<tiles, tc::kM, tc::kSmem, m->stream>>>(m->P, x, n, m->y, m->z, m->err);
   count_launch();
-  bwd_kernel<<<tiles, kW, kBwdSmem, m->stream>>>(m->P, x, t, m->y, m->z, n, 1.f / (float)n, m->gpart);
+  bwd_kernel<<<tiles, tc::kM, kBwdSmem, m->stream>>>(m->P, x, t, m->y, m->z, n, 1.f / (float)n, m->gpart,
+                                                      m->err);
   count_launch();
   reduce_kernel<<<(kPart + 255) / 256, 256, 0, m->stream>>>(m->gpart, tiles, m->grad);
   count_launch();
