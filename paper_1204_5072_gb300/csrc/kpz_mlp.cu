@@ -49,6 +49,8 @@ __device__ __forceinline__ float bf(const __nv_bfloat16* p, int i) { return __bf
 namespace tc {
 
 constexpr int kM = 128;                              // samples per tile (MMA M)
+constexpr int kQ = 4;                                // threads per sample: a quarter of the units each
+constexpr int kThreads = kM * kQ;                    // 16 warps; warp w reads tensor-memory lanes 32 (w % 4)
 constexpr uint32_t kOpBytes = (uint32_t)kW * kW * 2;  // one 128 x 128 bfloat16 operand
 constexpr size_t kSmem = 3 * (size_t)kOpBytes;       // A hi, A lo, W
 // Instruction descriptor of tcgen05.mma kind::f16: float32 accumulator
@@ -145,7 +147,7 @@ __device__ __forceinline__ void put8(unsigned char* Ahi, unsigned char* Alo, int
 // W (128 x 128 bfloat16, row = output unit, K contiguous) into the operand layout.
 __device__ __forceinline__ void stage_w(unsigned char* Bs, const __nv_bfloat16* W, int t) {
 #pragma unroll 4
-  for (int q = t; q < kW * kW / 8; q += kM) {
+  for (int q = t; q < kW * kW / 8; q += kThreads) {
     const int row = q >> 4, k0 = (q & 15) * 8;
     *reinterpret_cast<uint4*>(Bs + cm_off(row, k0)) = *reinterpret_cast<const uint4*>(W + row * kW + k0);
   }
@@ -161,17 +163,22 @@ __device__ __forceinline__ void fence_to_mma() {
 }  // namespace tc
 
 // Forward pass of a tile of 128 samples: y (and, for training, the
-// pre-activations z1..z3 in zsave).
-__global__ void __launch_bounds__(tc::kM, 1) fwd_kernel(const __nv_bfloat16* __restrict__ P,
-                                                        const float* __restrict__ x, int n, float* __restrict__ y,
-                                                        float* __restrict__ zsave, int* __restrict__ err) {
+// pre-activations z1..z3 in zsave). Thread (sample s, quarter q) handles units
+// 32 q .. 32 q + 31 of sample s; warps 4 q .. 4 q + 3 read columns 32 q ..
+// 32 q + 31 of the tensor-memory lanes of their samples.
+__global__ void __launch_bounds__(tc::kThreads, 1) fwd_kernel(const __nv_bfloat16* __restrict__ P,
+                                                              const float* __restrict__ x, int n,
+                                                              float* __restrict__ y, float* __restrict__ zsave,
+                                                              int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_tc[];
   unsigned char* Ahi = smem_tc;
   unsigned char* Alo = smem_tc + tc::kOpBytes;
   unsigned char* Bs = smem_tc + 2 * tc::kOpBytes;
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t taddr_s;
-  const int s = threadIdx.x, warp = s >> 5;
+  __shared__ float part[tc::kQ][tc::kM];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int s = (warp & 3) * 32 + (tid & 31), q = warp >> 2, u0 = 32 * q;
   const int gs = blockIdx.x * tc::kM + s;
   const bool live = gs < n;
   float xin[kIn];
@@ -179,7 +186,7 @@ __global__ void __launch_bounds__(tc::kM, 1) fwd_kernel(const __nv_bfloat16* __r
   for (int c = 0; c < kIn; ++c) xin[c] = live ? x[(size_t)gs * kIn + c] : 0.f;
   // Layer 1 (K = 4) on the CUDA cores, straight into the operand A.
 #pragma unroll 1
-  for (int j0 = 0; j0 < kW; j0 += 8) {
+  for (int j0 = u0; j0 < u0 + 32; j0 += 8) {
     float h[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -192,52 +199,50 @@ __global__ void __launch_bounds__(tc::kM, 1) fwd_kernel(const __nv_bfloat16* __r
     }
     tc::put8(Ahi, Alo, s, j0, h);
   }
-  tc::stage_w(Bs, P + oW2, s);
-  if (s == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&mbar)));
+  tc::stage_w(Bs, P + oW2, tid);
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&mbar)));
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(tc::smem_u32(&taddr_s)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   tc::fence_to_mma();
-  const uint32_t taddr = taddr_s, lanes = taddr + ((uint32_t)(warp * 32) << 16);
+  const uint32_t taddr = taddr_s, lanes = taddr + ((uint32_t)((warp & 3) * 32) << 16);
   const uint32_t mb = tc::smem_u32(&mbar);
   bool ok = true;
   const int oBl[2] = {oB2, oB3};
   float out = 0.f;
 #pragma unroll 1
   for (int layer = 0; layer < 2; ++layer) {
-    if (s == 0) tc::mma_chain(taddr, tc::smem_u32(Ahi), tc::smem_u32(Alo), tc::smem_u32(Bs), mb);
+    if (tid == 0) tc::mma_chain(taddr, tc::smem_u32(Ahi), tc::smem_u32(Alo), tc::smem_u32(Bs), mb);
     ok = tc::wait_phase(mb, (uint32_t)layer) && ok;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll 1
-    for (int c = 0; c < kW; c += 32) {
-      float v[32];
-      tc::ld32(lanes + (uint32_t)c, v);
+    float v[32];
+    tc::ld32(lanes + (uint32_t)u0, v);
 #pragma unroll
-      for (int g = 0; g < 32; g += 8) {
-        float h[8];
+    for (int g = 0; g < 32; g += 8) {
+      float h[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int j = c + g + i;
-          const float z = v[g + i] + bf(P + oBl[layer], j);
-          if (zsave && live) zsave[((size_t)gs * 3 + 1 + layer) * kW + j] = z;
-          h[i] = gelu(z);
-          if (layer == 1) out += bf(P + oW4, j) * h[i];
-        }
-        if (layer == 0) tc::put8(Ahi, Alo, s, c + g, h);
+      for (int i = 0; i < 8; ++i) {
+        const int j = u0 + g + i;
+        const float z = v[g + i] + bf(P + oBl[layer], j);
+        if (zsave && live) zsave[((size_t)gs * 3 + 1 + layer) * kW + j] = z;
+        h[i] = gelu(z);
+        if (layer == 1) out += bf(P + oW4, j) * h[i];
       }
+      if (layer == 0) tc::put8(Ahi, Alo, s, u0 + g, h);
     }
     if (layer == 0) {
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();   // every lane read layer 2 and the MMAs are done with W2: restage
-      tc::stage_w(Bs, P + oW3, s);
+      tc::stage_w(Bs, P + oW3, tid);
       tc::fence_to_mma();
     }
   }
-  if (live) y[gs] = out + bf(P + oB4, 0);
+  part[q][s] = out;
   if (!ok) atomicExch(err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (q == 0 && live) y[gs] = ((part[0][s] + part[1][s]) + part[2][s]) + part[3][s] + bf(P + oB4, 0);
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(taddr));
 }
 
@@ -279,7 +284,7 @@ __device__ __forceinline__ float get1(const unsigned char* Xhi, const unsigned c
 // operand layout: element (k, u) = W[u][k].
 __device__ __forceinline__ void stage_wt(unsigned char* Bs, const __nv_bfloat16* W, int t) {
 #pragma unroll 2
-  for (int q = t; q < kW * kW / 8; q += kM) {
+  for (int q = t; q < kW * kW / 8; q += kThreads) {
     const int k = q & (kW - 1), u0 = (q >> 7) * 8;
     __align__(16) __nv_bfloat16 v[8];
 #pragma unroll
@@ -297,13 +302,15 @@ __device__ __forceinline__ void stage_wt(unsigned char* Bs, const __nv_bfloat16*
 // split into bfloat16 hi and lo, three MMA chains hi.hi + hi.lo + lo.hi, in
 // tensor-memory columns 128..255) and the gradient at the layer's input
 // dh[s][k] = sum_u dz[s][u] W[u][k] (M = samples, K = units; two chains, in
-// columns 0..127). Column sums over the samples (biases, the output and the
-// first layer) are taken by one thread per unit in sample order.
-__global__ void __launch_bounds__(tc::kM, 1) bwd_kernel(const __nv_bfloat16* __restrict__ P,
-                                                        const float* __restrict__ x, const float* __restrict__ t,
-                                                        const float* __restrict__ y, const float* __restrict__ zsave,
-                                                        int n, float inv_n, float* __restrict__ gpart,
-                                                        int* __restrict__ err) {
+// columns 0..127). Thread (sample s, quarter q) handles units 32 q .. 32 q + 31
+// of sample s. Column sums over the samples (biases, the output and the first
+// layer) are taken per unit in four quarters of 32 samples, added in a fixed
+// order, so a call is deterministic.
+__global__ void __launch_bounds__(tc::kThreads, 1) bwd_kernel(const __nv_bfloat16* __restrict__ P,
+                                                              const float* __restrict__ x, const float* __restrict__ t,
+                                                              const float* __restrict__ y,
+                                                              const float* __restrict__ zsave, int n, float inv_n,
+                                                              float* __restrict__ gpart, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_tc[];
   unsigned char* X0 = smem_tc;                       // operand buffers, 32 KB each
   unsigned char* X1 = smem_tc + tc::kOpBytes;
@@ -312,27 +319,33 @@ __global__ void __launch_bounds__(tc::kM, 1) bwd_kernel(const __nv_bfloat16* __r
   float* dzT = reinterpret_cast<float*>(smem_tc);    // layer 1: dz1 as [unit][sample] float32 (X0, X1)
   __shared__ float dy[tc::kM];
   __shared__ float xs[tc::kM * kIn];
-  __shared__ float sq_part[tc::kM / 32];
+  __shared__ float sq_part[4];
+  __shared__ float red[tc::kQ][tc::kM][kIn + 1];     // per-quarter column sums
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t taddr_s;
-  const int s = threadIdx.x, warp = s >> 5;   // thread = sample s of the tile, or unit u = s
-  const int s0 = blockIdx.x * tc::kM, gs = s0 + s;
-  const bool live = gs < n;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int s = (warp & 3) * 32 + (tid & 31), q = warp >> 2, u0 = 32 * q;   // sample role
+  const int uu = tid & (tc::kM - 1), qq = tid >> 7, k0 = 32 * qq;            // unit role: unit uu, samples k0..k0+31
+  const int s0 = blockIdx.x * tc::kM;
   float* g = gpart + (size_t)blockIdx.x * kPart;
   auto zval = [&](int smp, int layer, int u) -> float {   // zero beyond the last sample
     return (s0 + smp < n) ? zsave[((size_t)(s0 + smp) * 3 + layer) * kW + u] : 0.f;
   };
+  // Sum of the four quarters' partials of unit uu (fixed order), by the threads of quarter 0.
+  auto combine = [&](int c) -> float { return ((red[0][uu][c] + red[1][uu][c]) + red[2][uu][c]) + red[3][uu][c]; };
+  if (q == 0) {
+    const int gs = s0 + s;
+    const bool live = gs < n;
 #pragma unroll
-  for (int c = 0; c < kIn; ++c) xs[s * kIn + c] = live ? x[(size_t)gs * kIn + c] : 0.f;
-  {
+    for (int c = 0; c < kIn; ++c) xs[s * kIn + c] = live ? x[(size_t)gs * kIn + c] : 0.f;
     const float r = live ? (y[gs] - t[gs]) : 0.f;
     dy[s] = 2.f * r * inv_n;
     float sq = r * r;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, d);
-    if ((s & 31) == 0) sq_part[warp] = sq;
+    if ((tid & 31) == 0) sq_part[warp] = sq;
   }
-  if (s == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&mbar)));
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&mbar)));
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(tc::smem_u32(&taddr_s)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -340,86 +353,92 @@ __global__ void __launch_bounds__(tc::kM, 1) bwd_kernel(const __nv_bfloat16* __r
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t taddr = taddr_s, lanes = taddr + ((uint32_t)(warp * 32) << 16);
+  const uint32_t taddr = taddr_s, lanes = taddr + ((uint32_t)((warp & 3) * 32) << 16);
   const uint32_t mb = tc::smem_u32(&mbar);
   const uint32_t x0 = tc::smem_u32(X0), x1 = tc::smem_u32(X1), x2 = tc::smem_u32(X2), x3 = tc::smem_u32(X3);
   uint32_t phase = 0;
   bool ok = true;
-  if (s == 0) g[kParams] = sq_part[0] + sq_part[1] + sq_part[2] + sq_part[3];
-  // Output layer (unit u = s): grads of w4 and b4, in sample order.
+  if (tid == 0) g[kParams] = ((sq_part[0] + sq_part[1]) + sq_part[2]) + sq_part[3];
+  // Output layer: grads of w4 and b4.
   {
     float gw4 = 0.f, gb = 0.f;
-    for (int k = 0; k < tc::kM; ++k) {
-      gw4 += dy[k] * gelu(zval(k, 2, s));
+#pragma unroll
+    for (int k = k0; k < k0 + 32; ++k) {
+      gw4 += dy[k] * gelu(zval(k, 2, uu));
       gb += dy[k];
     }
-    g[oW4 + s] = gw4;
-    if (s == 0) g[oB4] = gb;
+    red[qq][uu][0] = gw4;
+    red[qq][uu][1] = gb;
   }
+  __syncthreads();
+  if (qq == 0) {
+    g[oW4 + uu] = combine(0);
+    if (uu == 0) g[oB4] = combine(1);
+  }
+  __syncthreads();
   const int oW[2] = {oW3, oW2}, oB[2] = {oB3, oB2};
 #pragma unroll 1
   for (int L = 0; L < 2; ++L) {
     const int zl = 2 - L;   // pre-activation of this layer's output: z3, then z2
-    // dz (sample s) -> X0/X1 transposed (row = unit), h at the layer's input -> X2/X3 transposed.
-    // Layer 3: dz3 = dy w4 gelu'(z3); layer 2: dz2 = dh2 gelu'(z2), dh2 from tensor memory.
-#pragma unroll 1
-    for (int c = 0; c < kW; c += 32) {
+    // dz (sample s, units u0..u0+31) -> X0/X1 transposed (row = unit), h at the
+    // layer's input -> X2/X3 transposed. Layer 3: dz3 = dy w4 gelu'(z3); layer 2:
+    // dz2 = dh2 gelu'(z2), dh2 from tensor memory.
+    {
       float dh[32];
-      if (L == 1) tc::ld32(lanes + (uint32_t)c, dh);
-#pragma unroll
+      if (L == 1) tc::ld32(lanes + (uint32_t)u0, dh);
+#pragma unroll 16
       for (int i = 0; i < 32; ++i) {
-        const int u = c + i;
+        const int u = u0 + i;
         const float d = (L == 0) ? dy[s] * bf(P + oW4, u) : dh[i];
         tc::put1(X0, X1, u, s, d * gelu_grad(zval(s, zl, u)));
         tc::put1(X2, X3, u, s, gelu(zval(s, zl - 1, u)));
       }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     tc::fence_to_mma();
-    // Bias gradient (unit u = s): column sum of dz in sample order.
+    // Bias gradient: column sum of dz over the samples.
     {
       float db = 0.f;
-      for (int k = 0; k < tc::kM; ++k) db += tc::get1(X0, X1, s, k);
-      g[oB[L] + s] = db;
+#pragma unroll 8
+      for (int k = k0; k < k0 + 32; ++k) db += tc::get1(X0, X1, uu, k);
+      red[qq][uu][0] = db;
     }
     __syncthreads();   // every column read before X0/X1 are rewritten below
+    if (qq == 0) g[oB[L] + uu] = combine(0);
     // dW[u][k] into columns 128..255.
-    if (s == 0) {
+    if (tid == 0) {
       const uint32_t a[3] = {x0, x0, x1}, b[3] = {x2, x3, x2};
       tc::mma_pairs(taddr + 128u, a, b, 3, mb);
     }
     ok = tc::wait_phase(mb, phase) && ok;
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll 1
-    for (int c = 0; c < kW; c += 32) {
+    {
       float v[32];
-      tc::ld32(lanes + 128u + (uint32_t)c, v);
-      float* dst = g + oW[L] + s * kW + c;   // a tile's slot is not 16-byte aligned: scalar stores
+      tc::ld32(lanes + 128u + (uint32_t)u0, v);    // row = unit s, columns u0..u0+31
+      float* dst = g + oW[L] + s * kW + u0;        // a tile's slot is not 16-byte aligned: scalar stores
 #pragma unroll
       for (int i = 0; i < 32; ++i) dst[i] = v[i];
     }
     // dz again, now as rows (sample s) in X0/X1; W^T in X2.
-#pragma unroll 1
-    for (int c = 0; c < kW; c += 32) {
+    {
       float dh[32];
-      if (L == 1) tc::ld32(lanes + (uint32_t)c, dh);
+      if (L == 1) tc::ld32(lanes + (uint32_t)u0, dh);
 #pragma unroll
       for (int g8 = 0; g8 < 32; g8 += 8) {
         float d8[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          const int u = c + g8 + i;
+          const int u = u0 + g8 + i;
           const float d = (L == 0) ? dy[s] * bf(P + oW4, u) : dh[g8 + i];
           d8[i] = d * gelu_grad(zval(s, zl, u));
         }
-        tc::put8(X0, X1, s, c + g8, d8);
+        tc::put8(X0, X1, s, u0 + g8, d8);
       }
     }
-    tc::stage_wt(X2, P + oW[L], s);
+    tc::stage_wt(X2, P + oW[L], tid);
     tc::fence_to_mma();
     // dh at the layer's input into columns 0..127.
-    if (s == 0) {
+    if (tid == 0) {
       const uint32_t a[2] = {x0, x1}, b[2] = {x2, x2};
       tc::mma_pairs(taddr, a, b, 2, mb);
     }
@@ -429,27 +448,33 @@ __global__ void __launch_bounds__(tc::kM, 1) bwd_kernel(const __nv_bfloat16* __r
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
   }
-  // First layer: dz1 = dh1 gelu'(z1) (sample s) into dzT[u][s], then per unit u
-  // dW1[u][c] = sum_s dz1 x[s][c], db1[u] = sum_s dz1, in sample order.
-#pragma unroll 1
-  for (int c = 0; c < kW; c += 32) {
+  // First layer: dz1 = dh1 gelu'(z1) into dzT[u][s], then per unit
+  // dW1[u][c] = sum_s dz1 x[s][c], db1[u] = sum_s dz1.
+  {
     float dh[32];
-    tc::ld32(lanes + (uint32_t)c, dh);
+    tc::ld32(lanes + (uint32_t)u0, dh);
 #pragma unroll
-    for (int i = 0; i < 32; ++i) dzT[(c + i) * tc::kM + s] = dh[i] * gelu_grad(zval(s, 0, c + i));
+    for (int i = 0; i < 32; ++i) dzT[(u0 + i) * tc::kM + s] = dh[i] * gelu_grad(zval(s, 0, u0 + i));
   }
   __syncthreads();
   {
     float a[kIn] = {0.f, 0.f, 0.f, 0.f}, db = 0.f;
-    for (int k = 0; k < tc::kM; ++k) {
-      const float d = dzT[s * tc::kM + k];
+#pragma unroll 8
+    for (int k = k0; k < k0 + 32; ++k) {
+      const float d = dzT[uu * tc::kM + k];
       db += d;
 #pragma unroll
       for (int c = 0; c < kIn; ++c) a[c] += d * xs[k * kIn + c];
     }
 #pragma unroll
-    for (int c = 0; c < kIn; ++c) g[oW1 + s * kIn + c] = a[c];
-    g[oB1 + s] = db;
+    for (int c = 0; c < kIn; ++c) red[qq][uu][c] = a[c];
+    red[qq][uu][kIn] = db;
+  }
+  __syncthreads();
+  if (qq == 0) {
+#pragma unroll
+    for (int c = 0; c < kIn; ++c) g[oW1 + uu * kIn + c] = combine(c);
+    g[oB1 + uu] = combine(kIn);
   }
   if (!ok) atomicExch(err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -566,9 +591,9 @@ kpz_status ensure(kpz_mlp* m, size_t n, size_t w) {
 // data into m->grad; y and z are filled on the way.
 cudaError_t grad_pass(kpz_mlp* m, const float* x, const float* t, int n) {
   const int tiles = (n + tc::kM - 1) / tc::kM;
-  fwd_kernel<<<tiles, tc::kM, tc::kSmem, m->stream>>>(m->P, x, n, m->y, m->z, m->err);
+  fwd_kernel<<<tiles, tc::kThreads, tc::kSmem, m->stream>>>(m->P, x, n, m->y, m->z, m->err);
   count_launch();
-  bwd_kernel<<<tiles, tc::kM, kBwdSmem, m->stream>>>(m->P, x, t, m->y, m->z, n, 1.f / (float)n, m->gpart,
+  bwd_kernel<<<tiles, tc::kThreads, kBwdSmem, m->stream>>>(m->P, x, t, m->y, m->z, n, 1.f / (float)n, m->gpart,
                                                       m->err);
   count_launch();
   reduce_kernel<<<(kPart + 255) / 256, 256, 0, m->stream>>>(m->gpart, tiles, m->grad);
@@ -633,7 +658,7 @@ kpz_status kpz_mlp_predict(kpz_mlp* m, const float* x, uint32_t n, float* y) {
   if (st) return st;
   if (cudaMemcpyAsync(m->x, x, (size_t)n * kIn * 4, cudaMemcpyHostToDevice, m->stream) != cudaSuccess)
     return KPZ_ECUDA;
-  fwd_kernel<<<(n + tc::kM - 1) / tc::kM, tc::kM, tc::kSmem, m->stream>>>(m->P, m->x, (int)n, m->y, nullptr,
+  fwd_kernel<<<(n + tc::kM - 1) / tc::kM, tc::kThreads, tc::kSmem, m->stream>>>(m->P, m->x, (int)n, m->y, nullptr,
                                                                          m->err);
   count_launch();
   if (cudaGetLastError() != cudaSuccess ||
