@@ -34,8 +34,9 @@ __device__ __forceinline__ float gelu_grad(float z) {
 __device__ __forceinline__ float bf(const __nv_bfloat16* p, int i) { return __bfloat162float(p[i]); }
 
 // ---------------------------------------------------------------------------
-// Forward pass on the 5th-generation tensor cores (tcgen05). A tile is 128
-// samples, one thread per sample. The two 128 x 128 layers run as
+// The 128 x 128 layers on the 5th-generation tensor cores (tcgen05). A tile
+// is 128 samples, four threads per sample (each a quarter of the units). In
+// the forward pass the two 128 x 128 layers run as
 // D[s][j] = sum_k A[s][k] W[j][k] with M = N = K = 128: A (activations) and W
 // (weights) in shared memory in the canonical K-major layout without swizzle
 // (8-row x 16-byte core matrices, 128 B apart along K, 2048 B apart along the
